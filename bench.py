@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the LES stage path: grid-point-stage updates per second.
+
+A step is one explicit 5-stage Runge-Kutta step (all stage kernels + boundary
+passes) over the whole grid; points x 5 stages x steps / time is the metric.
+Default workload: the paper-scale single jet, 384x256x144 points (~14.2M),
+FP64, Mach 1.4, TR 1, Re_D 1e5.  Inputs are far larger than L2 (several GB).
+
+--impl reference times the FP64 CPU oracle (the plain C transcription of the
+method) on a bounded sample of the same workload.  Under torchrun each rank
+runs an independent replica of the workload (no data exchange); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2212_12365_gb300 import inputs as I  # noqa: E402
+
+# Algorithmic FP64/FP32 operations per grid point and stage, counted from the
+# method (each interface flux once; FMA = 2, divide/sqrt = 1): see the design
+# notes, section "Roofline".
+FLOPS_PER_PT_STAGE = {"prims": 90, "grads": 125, "flux": 947}
+# Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "jet-384x256x144": (I.jet_paper_scale, "fp64"),
+    "jet-768x384x192": (I.jet_large, "fp32"),
+    "jet-48x32x32": (I.jet_small, "fp64"),
+}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(spec, fp, budget_s=12.0, steps=1):
+    """The oracle as it stands on a bounded k-slab of the workload: one RK step
+    (5 stages); the slab grows until the run takes ~budget_s."""
+    import oracle
+
+    def to_oracle(sp, f):
+        g = oracle.Grid(x=sp.x, y=sp.y, z=sp.z, dims=tuple(sp.dims), periodic=tuple(sp.periodic),
+                        shift=np.asarray(sp.shift), bc=tuple(sp.bc))
+        return g, oracle.Params(**{k: getattr(f, k) for k in oracle.Params.__dataclass_fields__})
+
+    ni, nj, nk = spec.dims
+    nplanes = 4
+    best = None
+    while True:
+        k0 = max(0, nk // 2 - nplanes // 2)
+        slab = I.jet_slab(spec, k0, k0 + nplanes)
+        g, p = to_oracle(slab, fp)
+        m = oracle.metrics(g)
+        q = oracle.apply_bc(g, p, m, oracle.qhat_from(g, p, m, I.ambient_primitives(g.N, fp.TR), True), 0)
+        dt = oracle.dt_cfl(g, p, m, q)
+        t0 = time.perf_counter()
+        oracle.step(g, p, m, q, steps, 0, dt)
+        el = time.perf_counter() - t0
+        best = (g.N * 5 * steps / el, el, nplanes)
+        if el > budget_s / 4 or nplanes * 2 > nk:
+            break
+        nplanes *= 2
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": best[0], "unit": "grid-point-stage updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} RK step(s) on a {ni}x{nj}x{best[2]} k-slab of the workload "
+                      f"({best[1]:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    make, prec = WORKLOADS[args.workload]
+    spec, fp = make()
+    import oracle  # noqa: F401
+    oracle.build()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(spec, fp, budget_s=4.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(spec, fp, budget_s=8.0))
+    el = time.perf_counter() - t0
+    v = float(np.median([c["value"] for c in vals]))
+    line = {"impl": "reference", "metric": "grid-point-stage updates/s", "value": v,
+            "unit": "grid-point-stage updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "precision": "fp64", "points": spec.N},
+            "cpu_baseline": {**vals[0], "value": v},
+            "e2e": {"value": v, "unit": "grid-point-stage updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2212_12365_gb300 import build, les
+    build.build()
+    make, prec_default = WORKLOADS[args.workload]
+    prec = args.precision or prec_default
+    P = les.LES_FP64 if prec == "fp64" else les.LES_FP32
+    spec, fp = make()
+    fp.seed = fp.seed + 1000 * rank
+    N = spec.N
+    prim = I.ambient_primitives(N, fp.TR)
+    stream = torch.cuda.current_stream()
+    solver = les.Solver(spec, fp, P, stream=les.ctypes.c_void_p(stream.cuda_stream))
+    solver.set_state(prim, les.LES_STATE_PRIMITIVE)
+    # a developed state: march the start-up before timing
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        solver.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = les.les_last_launch_count(solver.h)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * 5 * args.steps / (ms / 1e3)
+
+    # per-kernel device time of the same stage sequence, eager with events
+    prof = les.les_profile_step(solver.h, max(1, min(args.steps, 3)))
+    tot = sum(v[0] for v in prof.values())
+    dom = max(("prims", "grads", "flux"), key=lambda k: prof[k][0])
+    t_launch = prof[dom][0] / max(prof[dom][1], 1) / 1e3  # s per launch
+    flops = FLOPS_PER_PT_STAGE[dom] * N
+    peaks = measured_peaks()
+    if prec == "fp64":
+        peak = FP64_PEAK_TFLOPS
+    else:
+        peak = FP32_PEAK_TFLOPS
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": flops / t_launch / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": flops / t_launch / 1e12 / peak,
+                "traffic": None,
+                "peak_source": f"nominal {'FP64' if prec == 'fp64' else 'FP32'} unit count x 2.07 GHz",
+                "share": prof[dom][0] / tot if tot else None,
+                "per_kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+                "hbm_gbs_measured_peak": peaks.get("hbm_gbs")}
+
+    # end to end through the public API: pinned host state in, step, state out
+    e2e = None
+    if not args.no_e2e and ws == 1:
+        host_in = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
+        host_in.numpy()[:] = solver.get_state(les.LES_STATE_RAW)
+        ke = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(ke):
+            les.lib().les_set_state_jet(solver.h, 0, les._dptr(host_in.numpy()), les.LES_STATE_RAW)
+            solver.step(1)
+            les.lib().les_get_state_jet(solver.h, 0, les._dptr(host_out.numpy()), les.LES_STATE_RAW)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ems = ev0.elapsed_time(ev1)
+        e2e = {"value": N * 5 * ke / (ems / 1e3), "unit": "grid-point-stage updates/s",
+               "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8, "steps": ke}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, fp)
+
+    solver.close()
+    if rank == 0:
+        line = {"metric": "grid-point-stage updates/s", "value": value,
+                "unit": "grid-point-stage updates/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "precision": prec, "points": N,
+                           "grid": list(spec.dims), "mach_j": fp.mach_j, "TR": fp.TR, "Re_D": fp.Re,
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (state + metrics + scratch are GBs)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="jet-384x256x144", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

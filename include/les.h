@@ -1,0 +1,218 @@
+/*
+ * les.h — C ABI of libles.so, a single-GPU (sm_103a) implementation of the
+ * per-stage residual evaluation and Runge-Kutta update of the filtered
+ * compressible Navier-Stokes LES of Junqueira-Junior, Yamouni, Azevedo &
+ * Wolf, "Large Eddy Simulations of Supersonic Jet Flows for Aeroacoustic
+ * Applications" (AIAA 2015, arXiv:2212.12365).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Jet units (Sec. "Dimensionless Formulation"): lengths in jet diameters
+ *   D, velocities in jet sound speed a_j, density in rho_j, temperature in
+ *   T_j; hence p = rho T / gamma, c^2 = T, Cp = 1/(gamma-1).
+ * - Grids are structured with ni x nj x nk points; host arrays are dense,
+ *   point (i,j,k) at linear index (k*nj + j)*ni + i (i = xi = axial fastest).
+ *   Field arrays of 5 variables are [field][point] (5*N doubles).
+ * - The stored state is Qhat = J^-1 [rho, rho u, rho v, rho w, e]
+ *   (Eq. hat_Q_vec); the API exchanges the unscaled Q, primitives
+ *   (rho, u, v, w, p), or the raw stored Qhat.
+ * - Every function returns LES_OK (0) or a negative LES_ERR_* code; the text
+ *   of the last error of a handle is returned by les_last_error().  A
+ *   NULL handle or pointer where one is required gives LES_ERR_ARG.  CUDA
+ *   failures give LES_ERR_CUDA and leave the handle usable only for
+ *   les_destroy().  No entry point waits on the device without bound.
+ * - Ownership: host arrays passed in are read (or written) during the call
+ *   only; the library copies what it keeps.  Device buffers passed in
+ *   (workspace, probe output) are borrowed: the caller keeps them alive
+ *   until les_destroy() (workspace) or until the probe is re-registered.
+ * - Streams: all device work of a handle runs on the cudaStream_t given at
+ *   creation (NULL = legacy default stream).  les_step() is asynchronous;
+ *   functions returning host data synchronise that stream.
+ */
+#ifndef LES_H
+#define LES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define LES_OK 0
+#define LES_ERR_ARG (-1)       /* invalid argument or unsupported combination */
+#define LES_ERR_OOM (-2)       /* device allocation failed / workspace too small */
+#define LES_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define LES_ERR_NONFINITE (-4) /* diagnostics found NaN/Inf in the state or residual */
+#define LES_ERR_TIMEOUT (-5)   /* reserved: no device-side wait exists in this library */
+#define LES_ERR_STATE (-6)     /* call out of order (e.g. step before set_state) */
+
+/* Face boundary conditions (Sec. "Boundary Conditions").  Faces are ordered
+ * i-, i+, j-, j+, k-, k+.  PERIODIC must be set on both faces of an axis
+ * declared periodic and nowhere else.  INFLOW_JET is allowed on the i- face
+ * only (jet axis along x at y = z = 0). */
+#define LES_BC_PERIODIC 0   /* Sec. "Periodic Boundary Condition", modulo indexing */
+#define LES_BC_FARFIELD 1   /* Sec. "Far Field Boundary", Riemann invariants */
+#define LES_BC_INFLOW_JET 2 /* Sec. "Entrance Boundary", supersonic jet + far field */
+#define LES_BC_EXIT 3       /* Sec. "Exit Boundary Condition" */
+
+/* Storage / arithmetic precision of the stencil path. Metrics and the
+ * Jacobian are always computed in FP64; diagnostics sum in FP64. */
+#define LES_FP64 0
+#define LES_FP32 1
+
+/* State kinds for les_set_state / les_get_state. */
+#define LES_STATE_CONSERVED 0 /* unscaled Q = [rho, rho u, rho v, rho w, e] */
+#define LES_STATE_PRIMITIVE 1 /* [rho, u, v, w, p] */
+#define LES_STATE_RAW 2       /* stored Qhat = J^-1 Q, for bit-exact checkpoints */
+
+/* Point fields for les_debug_field. */
+#define LES_FIELD_MU_SGS 0   /* Smagorinsky mu_sgs (Sec. "Subgrid Scale Viscosity") */
+#define LES_FIELD_MU 1       /* Sutherland mu/mu_j (Eq. sutherland) */
+#define LES_FIELD_P 2        /* pressure */
+#define LES_FIELD_T 3        /* temperature T/T_j */
+#define LES_FIELD_LAMBDA_XI 4   /* lambda-bar along xi (Turkel-Vatsa scaling) */
+#define LES_FIELD_LAMBDA_ETA 5
+#define LES_FIELD_LAMBDA_ZETA 6
+#define LES_FIELD_METRICS 7  /* 10 x N: J^-1 xi_x ... J^-1 zeta_z, J^-1 (FP64) */
+
+typedef struct les_grid_desc {
+    int ni, nj, nk;          /* points per axis; each >= 4 */
+    const double *x, *y, *z; /* host coordinates, ni*nj*nk each */
+    int periodic[3];         /* 1 if the axis is periodic (no duplicated point) */
+    double period_shift[3][3]; /* [axis][x,y,z]: coordinate offset of one period */
+    int face_bc[6];          /* LES_BC_* for faces i-, i+, j-, j+, k-, k+ */
+    int precision;           /* LES_FP64 or LES_FP32 */
+    void *workspace;         /* optional device memory for all buffers (NULL: the
+                                library allocates); borrowed, 256-byte aligned */
+    size_t workspace_bytes;  /* size of workspace (>= les_workspace_bytes()) */
+} les_grid_desc;
+
+typedef struct les_params {
+    double gamma;     /* specific heat ratio (1.4) */
+    double Pr;        /* Prandtl number (0.72) */
+    double Pr_sgs;    /* SGS Prandtl number (0.6, Eidson model) */
+    double Cs;        /* Smagorinsky constant (0.17) */
+    double k2, k4;    /* Turkel-Vatsa constants (0.25, 0.016) */
+    double Re;        /* rho_j a_j D / mu_j; INFINITY = inviscid */
+    double mach_j;    /* jet Mach number (>= 1 for LES_BC_INFLOW_JET) */
+    double TR;        /* T_j / T_inf (PR = 1: p_j = p_inf) */
+    double T_inf_dim; /* ambient temperature in K for Sutherland (288.15) */
+    double S1_dim;    /* Sutherland constant in K (110.4) */
+    double theta;     /* inflow momentum thickness in D (0.05) */
+    double noise_amp; /* inflow velocity noise amplitude / U_j (1e-3) */
+    double cfl;       /* CFL number for the time step (0.5) */
+    double dt;        /* fixed time step; 0 = from cfl at the first les_set_state */
+    uint64_t seed;    /* SplitMix64 seed of the inflow noise */
+} les_params;
+
+typedef struct les_diag {
+    double dt;                /* time step in use */
+    int64_t step;             /* completed steps (time level) */
+    double max_abs_rhs_rho;   /* L-inf of the continuity residual, interior points */
+    double l2_rhs[5];         /* sqrt(sum RHS_f^2) over interior points */
+    double sum_qhat[5];       /* sum of Qhat_f over all points (compensated FP64) */
+    int64_t nonfinite;        /* number of non-finite state/residual values */
+} les_diag;
+
+typedef struct les_handle les_handle;
+
+/* Bytes of device workspace les_create_grid needs for this grid (caller-
+ * provided workspace mode).  Returns 0 on invalid dimensions. */
+size_t les_workspace_bytes(const les_grid_desc *g);
+
+/* Create a solver for one grid (Secs. "Transformation of Coordinates",
+ * "Boundary Conditions").  Copies the coordinates to the device and computes
+ * the nine metric cofactors J^-1 d(xi,eta,zeta)/d(x,y,z) in conservative
+ * form and J^-1 in FP64.  stream: a cudaStream_t (NULL = default stream).
+ * On success *out owns all device memory of the solver until les_destroy.
+ * Errors: LES_ERR_ARG (dims < 4, inconsistent periodic/BC flags, INFLOW_JET
+ * off the i- face, Mach < 1 with INFLOW_JET, non-positive J^-1),
+ * LES_ERR_OOM, LES_ERR_CUDA. */
+int les_create_grid(const les_grid_desc *g, const les_params *p, void *stream, les_handle **out);
+
+/* Batched form: njets independent grids/parameter sets in one handle; every
+ * les_step advances all of them with one persistent launch per kernel of a
+ * stage.  Jet results are bit-identical to single-grid handles of the same
+ * precision.  Per-jet state access through les_set_state_jet etc. */
+int les_create_batch(const les_grid_desc *g, const les_params *p, int njets, void *stream,
+                     les_handle **out);
+
+/* Set the state of jet 0 (or of jet `jet`).  q: host array 5*N of `kind`
+ * (LES_STATE_*).  Applies the boundary conditions of the current time level
+ * (level 0 carries no inflow noise) and, if no time step is fixed yet,
+ * sets dt = cfl / max(lambda_xi + lambda_eta + lambda_zeta) over the state
+ * (Sec. "Numerical Formulation", spectral radii).  Synchronises the stream.
+ * Errors: LES_ERR_ARG (bad kind/jet), LES_ERR_CUDA. */
+int les_set_state(les_handle *h, const double *q, int kind);
+int les_set_state_jet(les_handle *h, int jet, const double *q, int kind);
+
+/* Advance every jet by nsteps steps of the 5-stage Runge-Kutta scheme
+ * (Eq. localdt, alpha = 1/4, 1/6, 3/8, 1/2, 1); after each stage of step
+ * n -> n+1 the boundary conditions of level n+1 are applied (faces y, z, x).
+ * One step is captured once as a CUDA graph and replayed.  Asynchronous on
+ * the handle's stream.  Errors: LES_ERR_STATE (no state set), LES_ERR_CUDA. */
+int les_step(les_handle *h, int nsteps);
+
+/* Copy the state of jet 0 / jet `jet` to the host array q (5*N, `kind`).
+ * Synchronises the stream. */
+int les_get_state(les_handle *h, double *q, int kind);
+int les_get_state_jet(les_handle *h, int jet, double *q, int kind);
+
+/* Time level and time step (checkpoint/resume): les_set_time fixes both;
+ * a following les_set_state with LES_STATE_RAW resumes bit-identically. */
+int les_set_time(les_handle *h, int64_t step, double dt);
+int les_get_time(les_handle *h, int64_t *step, double *dt);
+
+/* Register a surface probe on jet 0 (FW-H input surface): npts points xyz
+ * (host, 3*npts: all x, then all y, then all z).  After every step whose
+ * time level is a multiple of every_n, rho, u, v, w, p at the points are
+ * interpolated trilinearly from the 8 surrounding grid points and written to
+ * frame f = (count % capacity) of dev_out, a device array of
+ * out_capacity_frames * 5 * npts elements of the state precision (float or
+ * double), layout [frame][field][point]; count counts frames from
+ * registration.  The grid must be a Cartesian product (x = x(i), y = y(j),
+ * z = z(k)).  npts = 0 removes the probe.  Errors: LES_ERR_ARG (non-product
+ * grid, point outside the grid, every_n < 1). */
+int les_probe_surface(les_handle *h, const double *xyz, int npts, int every_n, void *dev_out,
+                      int out_capacity_frames);
+/* Frames written since registration. */
+int les_probe_frames(les_handle *h, int64_t *frames);
+
+/* Residual monitor of jet 0 / jet `jet` (Sec. "Computational Performance
+ * Assessment": max |RHS| of continuity) and conservation sums, computed from
+ * the current state.  Returns LES_ERR_NONFINITE if any state or residual
+ * value is NaN/Inf (d is still filled).  Synchronises the stream. */
+int les_get_diagnostics(les_handle *h, les_diag *d);
+int les_get_diagnostics_jet(les_handle *h, int jet, les_diag *d);
+
+/* Test access: RHS (5*N doubles, zero at boundary points) of the current
+ * state (Eq. spatial_discret), and point fields LES_FIELD_* (N doubles; 10*N
+ * for LES_FIELD_METRICS). */
+int les_debug_rhs(les_handle *h, int jet, double *rhs);
+int les_debug_field(les_handle *h, int jet, int field, double *out);
+
+/* Tracing: run nsteps steps eagerly (not from the graph) with CUDA events
+ * around every kernel launch on the handle's stream, and accumulate the
+ * device time per kernel kind into ms_out[LES_KERNEL_KINDS] (milliseconds,
+ * summed over launches) and the launch counts into counts (may be NULL).
+ * The state advances exactly as with les_step.  Synchronises the stream. */
+#define LES_KERNEL_PRIMS 0  /* primitives, Sutherland, lambda-bar */
+#define LES_KERNEL_GRADS 1  /* derivatives, Smagorinsky mu_sgs */
+#define LES_KERNEL_FLUX 2   /* interface fluxes, residual, stage update */
+#define LES_KERNEL_BC 3     /* boundary faces */
+#define LES_KERNEL_OTHER 4  /* time-level counter, probe */
+#define LES_KERNEL_KINDS 5
+int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts);
+
+/* Kernel launches issued by the most recent les_step call (all steps). */
+int64_t les_last_launch_count(les_handle *h);
+
+const char *les_last_error(les_handle *h);
+int les_destroy(les_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LES_H */

@@ -1,0 +1,1067 @@
+// CUDA kernels of libles.so (sm_103a).
+//
+// One Runge-Kutta stage (Sec. "Time Marching Method", Eq. localdt) runs as
+//   k_prims  : per point, primitives (Sec. LES formulation: EOS, Sutherland),
+//              spectral-radius scaling lambda-bar (Sec. Numerical Formulation)
+//   k_grads  : per point, computational velocity/temperature derivatives and
+//              the Smagorinsky eddy viscosity (Sec. Subgrid Scale Modeling)
+//   k_flux   : per interior point, the six interface fluxes (centred inviscid
+//              flux, Turkel-Vatsa dissipation, compact viscous + SGS flux),
+//              their differences (Eq. spatial_discret) and the stage update
+//   k_bc     : boundary faces of one axis (Sec. Boundary Conditions); launched
+//              for y, then z, then x
+// All kernels are persistent grid-stride loops over a block map that spans one
+// or many jets (batched form); the per-point arithmetic does not depend on the
+// map, so a jet gives the same bits alone or in a batch.
+#include <cmath>
+#include <cstdint>
+
+#include "les_internal.cuh"
+
+namespace les {
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+// Unit stencil of a second-order first derivative along one axis with
+// Delta xi = 1: central, or one-sided 3-point at the ends of a non-periodic
+// axis.  off[] are index offsets, wgt[] the weights.
+struct Stencil {
+    int n;
+    int off[3];
+    double wgt[3];
+};
+
+__device__ __forceinline__ Stencil deriv_stencil(int q, int n, int periodic)
+{
+    Stencil s;
+    if (periodic || (q > 0 && q < n - 1)) {
+        s.n = 2;
+        s.off[0] = -1; s.wgt[0] = -0.5;
+        s.off[1] = 1;  s.wgt[1] = 0.5;
+        s.off[2] = 0;  s.wgt[2] = 0.0;
+    } else if (q == 0) {
+        s.n = 3;
+        s.off[0] = 0; s.wgt[0] = -1.5;
+        s.off[1] = 1; s.wgt[1] = 2.0;
+        s.off[2] = 2; s.wgt[2] = -0.5;
+    } else {
+        s.n = 3;
+        s.off[0] = 0;  s.wgt[0] = 1.5;
+        s.off[1] = -1; s.wgt[1] = -2.0;
+        s.off[2] = -2; s.wgt[2] = 0.5;
+    }
+    return s;
+}
+
+__device__ __forceinline__ int floordiv_i(int a, int n)
+{
+    int q = a / n;
+    return (a % n != 0 && a < 0) ? q - 1 : q;
+}
+
+// ---------------------------------------------------------------------------
+// Metric terms (FP64), Sec. "Transformation of Coordinates"
+// ---------------------------------------------------------------------------
+
+struct CoordGrid {
+    const double *X[3];
+    int n[3];
+    int per[3];
+    double shift[9];
+};
+
+// Coordinate c at lattice point q; on periodic axes q may be outside [0,n) and
+// each crossed period adds the period shift (periodic extension of the grid).
+__device__ double coord_at(const CoordGrid &G, int c, int q0, int q1, int q2)
+{
+    int q[3] = {q0, q1, q2};
+    double off = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (G.per[a]) {
+            int w = floordiv_i(q[a], G.n[a]);
+            q[a] -= w * G.n[a];
+            off += w * G.shift[3 * a + c];
+        }
+    }
+    return G.X[c][((long long)q[2] * G.n[1] + q[1]) * G.n[0] + q[0]] + off;
+}
+
+// d x_c / d xi^a at lattice point q.
+__device__ double dcoord(const CoordGrid &G, int c, int a, const int q[3])
+{
+    // one-sided stencils are chosen from the wrapped index on periodic axes
+    Stencil s = deriv_stencil(q[a], G.n[a], G.per[a]);
+    double acc = 0.0;
+    for (int t = 0; t < s.n; ++t) {
+        int r[3] = {q[0], q[1], q[2]};
+        r[a] += s.off[t];
+        acc += s.wgt[t] * coord_at(G, c, r[0], r[1], r[2]);
+    }
+    return acc;
+}
+
+// D_outer [ x_c1 * D_inner x_c2 ] at lattice point q.
+__device__ double dprod(const CoordGrid &G, int c1, int c2, int inner, int outer, const int q[3])
+{
+    Stencil s = deriv_stencil(q[outer], G.n[outer], G.per[outer]);
+    double acc = 0.0;
+    for (int t = 0; t < s.n; ++t) {
+        int r[3] = {q[0], q[1], q[2]};
+        r[outer] += s.off[t];
+        acc += s.wgt[t] * coord_at(G, c1, r[0], r[1], r[2]) * dcoord(G, c2, inner, r);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, long long fs,
+                                                   int pitch, double Cs)
+{
+    long long total = (long long)G.n[0] * G.n[1] * G.n[2];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        q[0] = (int)(p % G.n[0]);
+        q[1] = (int)((p / G.n[0]) % G.n[1]);
+        q[2] = (int)(p / ((long long)G.n[0] * G.n[1]));
+        long long o = ((long long)q[2] * G.n[1] + q[1]) * pitch + q[0];
+        // conservative cofactors: J^-1 d xi^a / d x_c =
+        //   D_b( x_c1 D_d x_c2 ) - D_d( x_c1 D_b x_c2 ),  (a,b,d), (c,c1,c2) cyclic
+        for (int a = 0; a < 3; ++a) {
+            int b = (a + 1) % 3, d = (a + 2) % 3;
+            for (int c = 0; c < 3; ++c) {
+                int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                met[(3 * a + c) * fs + o] = dprod(G, c1, c2, d, b, q) - dprod(G, c1, c2, b, d, q);
+            }
+        }
+        double t[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 3; ++a) t[c][a] = dcoord(G, c, a, q);
+        // determinant of d(x,y,z)/d(xi,eta,zeta), as printed for 1/J
+        double jinv = t[0][0] * (t[1][1] * t[2][2] - t[1][2] * t[2][1]) -
+                      t[0][1] * (t[1][0] * t[2][2] - t[1][2] * t[2][0]) +
+                      t[0][2] * (t[1][0] * t[2][1] - t[1][1] * t[2][0]);
+        met[MET_JINV * fs + o] = jinv;
+        double delta = cbrt(jinv); // filter width: cube root of the cell volume
+        met[MET_CSD2 * fs + o] = (Cs * delta) * (Cs * delta);
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_convert_metrics(const double *met64, long long fs64,
+                                                           real *met, long long fs, long long npad)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npad;
+         p += (long long)gridDim.x * blockDim.x)
+        for (int f = 0; f < NMET; ++f) met[f * fs + p] = (real)met64[f * fs64 + p];
+}
+
+// ---------------------------------------------------------------------------
+// Point decomposition of a virtual block
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__device__ __forceinline__ bool point_of(const JetDev<real> &J, long long lp, int q[3])
+{
+    int i = (int)(lp % J.pitch);
+    long long r = lp / J.pitch;
+    q[0] = i;
+    q[1] = (int)(r % J.n[1]);
+    q[2] = (int)(r / J.n[1]);
+    return i < J.n[0] && q[2] < J.n[2];
+}
+
+template <typename real>
+__device__ __forceinline__ bool is_end(const JetDev<real> &J, int a, int qa)
+{
+    return !J.per[a] && (qa == 0 || qa == J.n[a] - 1);
+}
+
+template <typename real>
+__device__ __forceinline__ bool interior(const JetDev<real> &J, const int q[3])
+{
+    return !(is_end(J, 0, q[0]) || is_end(J, 1, q[1]) || is_end(J, 2, q[2]));
+}
+
+// ---------------------------------------------------------------------------
+// k_prims: primitives, Sutherland viscosity, lambda-bar
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_prims(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                                 int src)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        if (lp >= J.npts_pad) continue;
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        const real *Q = J.q[src];
+        const long long fs = J.fs;
+        const real gam = (real)J.gamma;
+        real jinv = J.met[MET_JINV * fs + lp];
+        real rj = real(1) / jinv;
+        real q0 = Q[lp];
+        real rq0 = real(1) / q0;
+        real rho = q0 * rj;
+        real u = Q[fs + lp] * rq0, v = Q[2 * fs + lp] * rq0, w = Q[3 * fs + lp] * rq0;
+        real e = Q[4 * fs + lp] * rj;
+        real p = (gam - real(1)) * (e - real(0.5) * rho * (u * u + v * v + w * w));
+        real T = gam * p / rho;
+        real S = (real)J.suth_S;
+        real mu = T * sqrt(T) * (real(1) + S) / (T + S);
+        real c = sqrt(T); // c^2 = gamma p / rho = T in jet units
+        real lam[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            real mx = J.met[(3 * a) * fs + lp], my = J.met[(3 * a + 1) * fs + lp],
+                 mz = J.met[(3 * a + 2) * fs + lp];
+            real U = (mx * u + my * v + mz * w) * rj;
+            lam[a] = fabs(U) + c * sqrt(mx * mx + my * my + mz * mz) * rj;
+        }
+        real s01 = sqrt(lam[0] * lam[1]), s02 = sqrt(lam[0] * lam[2]), s12 = sqrt(lam[1] * lam[2]);
+        real *P = J.prim;
+        P[P_RHO * fs + lp] = rho;
+        P[P_U * fs + lp] = u;
+        P[P_V * fs + lp] = v;
+        P[P_W * fs + lp] = w;
+        P[P_P * fs + lp] = p;
+        P[P_T * fs + lp] = T;
+        P[P_MU * fs + lp] = mu;
+        // lambda-bar_a = lambda_a [1 + (lambda_b/lambda_a)^1/2 + (lambda_d/lambda_a)^1/2]
+        P[P_LXI * fs + lp] = lam[0] + s01 + s02;
+        P[P_LETA * fs + lp] = lam[1] + s01 + s12;
+        P[P_LZETA * fs + lp] = lam[2] + s02 + s12;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_grads: computational derivatives of u, v, w, T and mu_sgs
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict__ jets, BlockMap bm)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        if (lp >= J.npts_pad) continue;
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        const real *P = J.prim;
+        real d[4][3]; // d phi / d xi^a for phi = u, v, w, T
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Stencil s = deriv_stencil(q[a], J.n[a], J.per[a]);
+            long long o[3];
+            for (int t = 0; t < 3; ++t) {
+                int r[3] = {q[0], q[1], q[2]};
+                r[a] = J.per[a] ? wrapi(r[a] + s.off[t], J.n[a]) : r[a] + s.off[t];
+                o[t] = lidx(J, r[0], r[1], r[2]);
+            }
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const real *F = P + (P_U + f) * fs;
+                real acc = (real)s.wgt[0] * F[o[0]] + (real)s.wgt[1] * F[o[1]];
+                if (s.n == 3) acc += (real)s.wgt[2] * F[o[2]];
+                d[f][a] = acc;
+            }
+        }
+        real *G = J.grad;
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) G[(3 * f + a) * fs + lp] = d[f][a];
+        // velocity gradient d u_i / d x_c = J (sum_a (J^-1 d xi^a/d x_c) d u_i / d xi^a)
+        real m[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) m[t] = J.met[t * fs + lp];
+        real rj = real(1) / J.met[MET_JINV * fs + lp];
+        real gu[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gu[i][c] = (m[c] * d[i][0] + m[3 + c] * d[i][1] + m[6 + c] * d[i][2]) * rj;
+        real ss = real(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                real sic = real(0.5) * (gu[i][c] + gu[c][i]);
+                ss += sic * sic;
+            }
+        // Smagorinsky: mu_sgs = rho (Cs Delta)^2 (2 S_ij S_ij)^1/2
+        G[G_MUSGS * fs + lp] = P[P_RHO * fs + lp] * J.met[MET_CSD2 * fs + lp] * sqrt(real(2) * ss);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Interface flux (Eq. inv_flux_vec with Eq. dissip_term, minus the viscous
+// flux of Eqs. hat-flux-Ev/Fv/Gv) between point L and L + e_a.
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__device__ __noinline__ void interface_flux(const JetDev<real> &J, int a, int iL0, int iL1, int iL2,
+                                            real *H)
+{
+    const long long fs = J.fs;
+    const real *P = J.prim;
+    const real *G = J.grad;
+    const real *M = J.met;
+    int qL[3] = {iL0, iL1, iL2};
+    int qR[3] = {iL0, iL1, iL2};
+    qR[a] = J.per[a] ? wrapi(qL[a] + 1, J.n[a]) : qL[a] + 1;
+    const long long L = lidx(J, qL[0], qL[1], qL[2]);
+    const long long R = lidx(J, qR[0], qR[1], qR[2]);
+    const bool lo_end = !J.per[a] && qL[a] == 0;
+    const bool hi_end = !J.per[a] && qR[a] == J.n[a] - 1;
+    long long Lm = L, Rp = R;
+    if (!lo_end) {
+        int r[3] = {qL[0], qL[1], qL[2]};
+        r[a] = J.per[a] ? wrapi(qL[a] - 1, J.n[a]) : qL[a] - 1;
+        Lm = lidx(J, r[0], r[1], r[2]);
+    }
+    if (!hi_end) {
+        int r[3] = {qR[0], qR[1], qR[2]};
+        r[a] = J.per[a] ? wrapi(qR[a] + 1, J.n[a]) : qR[a] + 1;
+        Rp = lidx(J, r[0], r[1], r[2]);
+    }
+    const real gam = (real)J.gamma;
+    const real gm1 = gam - real(1);
+    const real hgam = gam / gm1;
+
+    // primitive values of the (up to) four points along the axis
+    real rho[4], u[4], v[4], w[4], p[4];
+    const long long idx4[4] = {Lm, L, R, Rp};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        long long o = idx4[t];
+        rho[t] = P[P_RHO * fs + o];
+        u[t] = P[P_U * fs + o];
+        v[t] = P[P_V * fs + o];
+        w[t] = P[P_W * fs + o];
+        p[t] = P[P_P * fs + o];
+    }
+    // dissipation vector W = [rho, rho u, rho v, rho w, e + p] (unscaled)
+    real W[4][5];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        W[t][0] = rho[t];
+        W[t][1] = rho[t] * u[t];
+        W[t][2] = rho[t] * v[t];
+        W[t][3] = rho[t] * w[t];
+        W[t][4] = hgam * p[t] + real(0.5) * rho[t] * (u[t] * u[t] + v[t] * v[t] + w[t] * w[t]);
+    }
+    // pressure sensors of L and R; an end point takes its interior neighbour's
+    real nuL, nuR;
+    {
+        real sL = fabs(p[2] - real(2) * p[1] + p[0]) / (p[2] + real(2) * p[1] + p[0]);
+        real sR = fabs(p[3] - real(2) * p[2] + p[1]) / (p[3] + real(2) * p[2] + p[1]);
+        nuL = lo_end ? sR : sL;
+        nuR = hi_end ? sL : sR;
+    }
+    const real eps2 = (real)J.k2 * fmax(nuL, nuR);
+    const real eps4 = fmax(real(0), (real)J.k4 - eps2);
+    const real lamL = P[(P_LXI + a) * fs + L], lamR = P[(P_LXI + a) * fs + R];
+    const real lam = real(0.5) * (lamL + lamR);
+    const real jinvL = M[MET_JINV * fs + L], jinvR = M[MET_JINV * fs + R];
+    const real jb = real(0.5) * (jinvL + jinvR);
+
+    // metric rows of L and R
+    real mL[9], mR[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        mL[t] = M[t * fs + L];
+        mR[t] = M[t * fs + R];
+    }
+    // centred inviscid flux 0.5 (F_L + F_R); J^-1 U = m_a . u
+    real Fc[5];
+    {
+        const real *ma = mL + 3 * a;
+        const real *mb = mR + 3 * a;
+        real JUL = ma[0] * u[1] + ma[1] * v[1] + ma[2] * w[1];
+        real JUR = mb[0] * u[2] + mb[1] * v[2] + mb[2] * w[2];
+        Fc[0] = real(0.5) * (rho[1] * JUL + rho[2] * JUR);
+        Fc[1] = real(0.5) * (W[1][1] * JUL + p[1] * ma[0] + W[2][1] * JUR + p[2] * mb[0]);
+        Fc[2] = real(0.5) * (W[1][2] * JUL + p[1] * ma[1] + W[2][2] * JUR + p[2] * mb[1]);
+        Fc[3] = real(0.5) * (W[1][3] * JUL + p[1] * ma[2] + W[2][3] * JUR + p[2] * mb[2]);
+        Fc[4] = real(0.5) * (W[1][4] * JUL + W[2][4] * JUR);
+    }
+    // Turkel-Vatsa dissipation with the boundary extrapolation of dW
+    real Dis[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        real dW0 = W[2][f] - W[1][f];
+        real dWp = hi_end ? -dW0 : W[3][f] - W[2][f];
+        real dWm = lo_end ? -dW0 : W[1][f] - W[0][f];
+        real d3 = dWp - real(2) * dW0 + dWm;
+        Dis[f] = jb * lam * (eps2 * dW0 - eps4 * d3);
+    }
+    // compact viscous + SGS flux
+    real Fv[5];
+    {
+        real dphi[4][3];
+        real phiL[4] = {u[1], v[1], w[1], P[P_T * fs + L]};
+        real phiR[4] = {u[2], v[2], w[2], P[P_T * fs + R]};
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                dphi[f][b] = (b == a) ? phiR[f] - phiL[f]
+                                      : real(0.5) * (G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R]);
+        real mc[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) mc[t] = real(0.5) * (mL[t] + mR[t]);
+        real rjb = real(1) / jb;
+        real gu[4][3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gu[f][c] = (mc[c] * dphi[f][0] + mc[3 + c] * dphi[f][1] + mc[6 + c] * dphi[f][2]) * rjb;
+        real div = gu[0][0] + gu[1][1] + gu[2][2];
+        real mu = real(0.5) * (P[P_MU * fs + L] + P[P_MU * fs + R]);
+        real mus = real(0.5) * (G[G_MUSGS * fs + L] + G[G_MUSGS * fs + R]);
+        real mure = mu / (real)J.Re;
+        real coef = real(2) * (mure + mus);
+        real tau[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                real s = real(0.5) * (gu[i][c] + gu[c][i]);
+                tau[i][c] = coef * (i == c ? s - div / real(3) : s);
+            }
+        real kap = mure / (gm1 * (real)J.Pr) + mus / (gm1 * (real)J.Pr_sgs);
+        real vb[3] = {real(0.5) * (u[1] + u[2]), real(0.5) * (v[1] + v[2]), real(0.5) * (w[1] + w[2])};
+        real beta[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            beta[i] = tau[i][0] * vb[0] + tau[i][1] * vb[1] + tau[i][2] * vb[2] + kap * gu[3][i];
+        const real *mr = mc + 3 * a;
+        Fv[0] = real(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Fv[1 + i] = mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
+        Fv[4] = mr[0] * beta[0] + mr[1] * beta[1] + mr[2] * beta[2];
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) H[f] = Fc[f] - Dis[f] - Fv[f];
+}
+
+__constant__ double c_rk_alpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
+
+// Stage update Q(dst) = Q(0) - alpha_stage dt RHS(prims of Q(src)), or (rhs_only)
+// RHS into J.rhs with zeros at boundary points.
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_flux(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                                int dst, int stage, const double *__restrict__ dt,
+                                                int rhs_only)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        if (lp >= J.npts_pad) continue;
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        if (!interior(J, q)) {
+            if (rhs_only)
+                for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = real(0);
+            continue;
+        }
+        real R[5] = {0, 0, 0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll 1
+            for (int s = 0; s < 2; ++s) {
+                int r[3] = {q[0], q[1], q[2]};
+                if (s == 0) r[a] = J.per[a] ? wrapi(q[a] - 1, J.n[a]) : q[a] - 1;
+                real H[5];
+                interface_flux<real>(J, a, r[0], r[1], r[2], H);
+                real sg = s == 0 ? real(-1) : real(1);
+#pragma unroll
+                for (int f = 0; f < 5; ++f) R[f] += sg * H[f];
+            }
+        }
+        if (rhs_only) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = R[f];
+        } else {
+            real adt = (real)(c_rk_alpha[stage] * dt[jet]);
+            const real *Q0 = J.q[0];
+            real *Qd = J.q[dst];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Qd[f * fs + lp] = Q0[f * fs + lp] - adt * R[f];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary conditions (FP64 arithmetic on the stored state)
+// ---------------------------------------------------------------------------
+
+struct Prim64 {
+    double rho, u[3], p;
+};
+
+__device__ __forceinline__ void cons_of(const Prim64 &s, double g, double Q[5])
+{
+    Q[0] = s.rho;
+    Q[1] = s.rho * s.u[0];
+    Q[2] = s.rho * s.u[1];
+    Q[3] = s.rho * s.u[2];
+    Q[4] = s.p / (g - 1.0) + 0.5 * s.rho * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+}
+
+__device__ __forceinline__ Prim64 prim_of(const double Q[5], double g)
+{
+    Prim64 s;
+    s.rho = Q[0];
+    for (int c = 0; c < 3; ++c) s.u[c] = Q[1 + c] / Q[0];
+    s.p = (g - 1.0) * (Q[4] - 0.5 * Q[0] * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]));
+    return s;
+}
+
+// Far field (Sec. "Far Field Boundary"): Riemann invariants along the unit
+// outward normal n; R- from the ambient at rest, R+ from the interior point.
+__device__ void bc_farfield(double g, double TR, const double Qe[5], const double n[3], double Qf[5])
+{
+    Prim64 e = prim_of(Qe, g);
+    const double pinf = 1.0 / g, rinf = TR;
+    const double ce = sqrt(g * e.p / e.rho), cinf = sqrt(g * pinf / rinf);
+    const double qne = e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2];
+    const double rp = qne + 2.0 * ce / (g - 1.0);
+    const double rm = 0.0 - 2.0 * cinf / (g - 1.0);
+    const double qnf = 0.5 * (rp + rm);
+    const double cf = 0.25 * (g - 1.0) * (rp - rm);
+    const double mn = qne / ce;
+    Prim64 f;
+    if (mn >= 1.0) {
+        for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
+        return;
+    }
+    if (mn <= -1.0) {
+        f.rho = rinf;
+        f.u[0] = f.u[1] = f.u[2] = 0.0;
+        f.p = pinf;
+        cons_of(f, g, Qf);
+        return;
+    }
+    if (mn >= 0.0) { // subsonic outflow: entropy and tangential velocity from inside
+        for (int c = 0; c < 3; ++c) f.u[c] = e.u[c] + (qnf - qne) * n[c];
+        f.rho = pow(pow(e.rho, g) * cf * cf / (g * e.p), 1.0 / (g - 1.0));
+    } else { // subsonic inflow: from the ambient (q_n,inf = 0)
+        for (int c = 0; c < 3; ++c) f.u[c] = 0.0 + (qnf - 0.0) * n[c];
+        f.rho = pow(pow(rinf, g) * cf * cf / (g * pinf), 1.0 / (g - 1.0));
+    }
+    f.p = f.rho * cf * cf / g;
+    cons_of(f, g, Qf);
+}
+
+// Exit (Sec. "Exit Boundary Condition").
+__device__ void bc_exit(double g, const double Qe[5], const double n[3], double Qf[5])
+{
+    Prim64 e = prim_of(Qe, g);
+    const double ce = sqrt(g * e.p / e.rho);
+    if ((e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2]) / ce >= 1.0) {
+        for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
+        return;
+    }
+    const double ei = e.p / ((g - 1.0) * e.rho);
+    const double rho = (1.0 / g) / ((g - 1.0) * ei);
+    Qf[0] = rho;
+    Qf[1] = rho * e.u[0];
+    Qf[2] = rho * e.u[1];
+    Qf[3] = rho * e.u[2];
+    Qf[4] = rho * (ei + 0.5 * (e.u[0] * e.u[0] + e.u[1] * e.u[1] + e.u[2] * e.u[2]));
+}
+
+// SplitMix64: output number n of the generator seeded with `seed`.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long n)
+{
+    unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                              int axis, int dst, const long long *__restrict__ level_p)
+{
+    const long long level = *level_p;
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        if (J.per[axis]) continue;
+        const int b = (axis + 1) % 3, d = (axis + 2) % 3;
+        const long long nface = (long long)J.n[b] * J.n[d];
+        long long t = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        if (t >= 2 * nface) continue;
+        const int side = (int)(t / nface);
+        const long long r = t - side * nface;
+        const int ib = (int)(r % J.n[b]), id = (int)(r / J.n[b]);
+        const int type = J.bc[2 * axis + side];
+        int qf[3], qe[3];
+        qf[axis] = side ? J.n[axis] - 1 : 0;
+        qe[axis] = side ? J.n[axis] - 2 : 1;
+        qf[b] = qe[b] = ib;
+        qf[d] = qe[d] = id;
+        const long long F = lidx(J, qf[0], qf[1], qf[2]);
+        const long long E = lidx(J, qe[0], qe[1], qe[2]);
+        const long long fs = J.fs;
+        real *Qd = J.q[dst];
+        const double g = J.gamma;
+        // unit outward normal from the face point's metric row
+        double n[3], nn = 0.0;
+        const double sg = side ? 1.0 : -1.0;
+        for (int c = 0; c < 3; ++c) {
+            n[c] = sg * (double)J.met[(3 * axis + c) * fs + F];
+            nn += n[c] * n[c];
+        }
+        nn = sqrt(nn);
+        for (int c = 0; c < 3; ++c) n[c] /= nn;
+        const double jinvE = J.jinv64[E], jinvF = J.jinv64[F];
+        double Qe[5], Qf[5];
+        for (int f = 0; f < 5; ++f) Qe[f] = (double)Qd[f * fs + E] / jinvE;
+        if (type == LES_BC_FARFIELD) {
+            bc_farfield(g, J.TR, Qe, n, Qf);
+        } else if (type == LES_BC_EXIT) {
+            bc_exit(g, Qe, n, Qf);
+        } else if (type == LES_BC_INFLOW_JET) {
+            const int jj = qf[1], kk = qf[2];
+            const double rr = J.inflow_r[(long long)kk * J.n[1] + jj];
+            const double ut = 0.5 * (1.0 + tanh((0.5 - rr) / (2.0 * J.theta)));
+            if (ut < 0.01) {
+                bc_farfield(g, J.TR, Qe, n, Qf);
+            } else {
+                const double M = J.mach;
+                const double T = (1.0 / J.TR) * (1.0 - ut) + ut + 0.5 * (g - 1.0) * M * M * ut * (1.0 - ut);
+                Prim64 s;
+                s.p = 1.0 / g;
+                s.rho = g * s.p / T;
+                s.u[0] = M * ut;
+                s.u[1] = s.u[2] = 0.0;
+                if (level > 0) {
+                    for (int c = 0; c < 3; ++c) {
+                        unsigned long long ctr =
+                            ((((unsigned long long)(level - 1) * (unsigned long long)J.n[2] +
+                               (unsigned long long)kk) * (unsigned long long)J.n[1] +
+                              (unsigned long long)jj) * 3ull) + (unsigned long long)c;
+                        double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
+                        s.u[c] += J.noise_amp * M * (2.0 * h - 1.0);
+                    }
+                }
+                cons_of(s, g, Qf);
+            }
+        } else {
+            continue;
+        }
+        for (int f = 0; f < 5; ++f) Qd[f * fs + F] = (real)(jinvF * Qf[f]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// State conversion (host dense FP64 <-> device padded Qhat)
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_set_state(const JetDev<real> *__restrict__ jets, int jet,
+                                                     const double *__restrict__ in, int kind)
+{
+    const JetDev<real> &J = jets[jet];
+    const long long N = (long long)J.n[0] * J.n[1] * J.n[2];
+    for (long long lp = blockIdx.x * (long long)blockDim.x + threadIdx.x; lp < J.npts_pad;
+         lp += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        long long dense = ((long long)q[2] * J.n[1] + q[1]) * J.n[0] + q[0];
+        double v[5];
+        for (int f = 0; f < 5; ++f) v[f] = in[f * N + dense];
+        real *Q = J.q[0];
+        if (kind == LES_STATE_RAW) {
+            for (int f = 0; f < 5; ++f) Q[f * J.fs + lp] = (real)v[f];
+            continue;
+        }
+        double Qc[5];
+        if (kind == LES_STATE_PRIMITIVE) {
+            Prim64 s;
+            s.rho = v[0];
+            s.u[0] = v[1];
+            s.u[1] = v[2];
+            s.u[2] = v[3];
+            s.p = v[4];
+            cons_of(s, J.gamma, Qc);
+        } else {
+            for (int f = 0; f < 5; ++f) Qc[f] = v[f];
+        }
+        const double jinv = J.jinv64[lp];
+        for (int f = 0; f < 5; ++f) Q[f * J.fs + lp] = (real)(jinv * Qc[f]);
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_get_state(const JetDev<real> *__restrict__ jets, int jet,
+                                                     double *__restrict__ out, int kind)
+{
+    const JetDev<real> &J = jets[jet];
+    const long long N = (long long)J.n[0] * J.n[1] * J.n[2];
+    for (long long lp = blockIdx.x * (long long)blockDim.x + threadIdx.x; lp < J.npts_pad;
+         lp += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        long long dense = ((long long)q[2] * J.n[1] + q[1]) * J.n[0] + q[0];
+        const real *Q = J.q[0];
+        double v[5];
+        for (int f = 0; f < 5; ++f) v[f] = (double)Q[f * J.fs + lp];
+        if (kind != LES_STATE_RAW) {
+            const double jinv = J.jinv64[lp];
+            for (int f = 0; f < 5; ++f) v[f] /= jinv;
+            if (kind == LES_STATE_PRIMITIVE) {
+                Prim64 s = prim_of(v, J.gamma);
+                v[0] = s.rho;
+                v[1] = s.u[0];
+                v[2] = s.u[1];
+                v[3] = s.u[2];
+                v[4] = s.p;
+            }
+        }
+        for (int f = 0; f < 5; ++f) out[f * N + dense] = v[f];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Time step: max over points of lambda_xi + lambda_eta + lambda_zeta
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_dt_max(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                                  unsigned long long *maxbits)
+{
+    __shared__ double red[BLOCK];
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        double val = 0.0;
+        int q[3];
+        if (lp < J.npts_pad && point_of(J, lp, q)) {
+            const long long fs = J.fs;
+            double rj = 1.0 / (double)J.met[MET_JINV * fs + lp];
+            double u = J.prim[P_U * fs + lp], v = J.prim[P_V * fs + lp], w = J.prim[P_W * fs + lp];
+            double c = sqrt((double)J.prim[P_T * fs + lp]);
+            for (int a = 0; a < 3; ++a) {
+                double mx = J.met[(3 * a) * fs + lp], my = J.met[(3 * a + 1) * fs + lp],
+                       mz = J.met[(3 * a + 2) * fs + lp];
+                val += fabs((mx * u + my * v + mz * w) * rj) + c * sqrt(mx * mx + my * my + mz * mz) * rj;
+            }
+        }
+        red[threadIdx.x] = val;
+        __syncthreads();
+        for (int s = BLOCK / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            atomicMax(maxbits + jet, (unsigned long long)__double_as_longlong(red[0]));
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: per-block partials in a fixed order, then one block combines.
+// partial layout (16 doubles): [0] max|RHS_rho|, [1..5] sum RHS^2,
+// [6..10] Neumaier sums of Qhat, [11..15] their compensations; nonfinite
+// count is folded into [0] as NaN.
+// ---------------------------------------------------------------------------
+
+constexpr int NPART = 17;
+
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double v)
+{
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_diag_partials(const JetDev<real> *__restrict__ jets,
+                                                         int jet, double *partials)
+{
+    const JetDev<real> &J = jets[jet];
+    __shared__ double sh[NPART][BLOCK];
+    double mx = 0.0, l2[5] = {0, 0, 0, 0, 0}, s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
+    double bad = 0.0;
+    const long long fs = J.fs;
+    for (long long lp = blockIdx.x * (long long)blockDim.x + threadIdx.x; lp < J.npts_pad;
+         lp += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        for (int f = 0; f < 5; ++f) {
+            double r = (double)J.rhs[f * fs + lp];
+            double v = (double)J.q[0][f * fs + lp];
+            if (!isfinite(r) || !isfinite(v)) bad += 1.0;
+            l2[f] += r * r;
+            neumaier_add(s[f], c[f], v);
+        }
+        mx = fmax(mx, fabs((double)J.rhs[lp]));
+    }
+    sh[0][threadIdx.x] = mx;
+    for (int f = 0; f < 5; ++f) {
+        sh[1 + f][threadIdx.x] = l2[f];
+        sh[6 + f][threadIdx.x] = s[f];
+        sh[11 + f][threadIdx.x] = c[f];
+    }
+    sh[16][threadIdx.x] = bad;
+    __syncthreads();
+    for (int st = BLOCK / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            int o = threadIdx.x + st;
+            sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][o]);
+            for (int f = 0; f < 5; ++f) {
+                sh[1 + f][threadIdx.x] += sh[1 + f][o];
+                double a = sh[6 + f][threadIdx.x], ca = sh[11 + f][threadIdx.x];
+                neumaier_add(a, ca, sh[6 + f][o]);
+                sh[6 + f][threadIdx.x] = a;
+                sh[11 + f][threadIdx.x] = ca + sh[11 + f][o];
+            }
+            sh[16][threadIdx.x] += sh[16][o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < NPART) partials[blockIdx.x * NPART + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(const double *partials, int nblocks, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mx = 0.0, l2[5] = {0, 0, 0, 0, 0}, s[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0}, bad = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double *P = partials + b * NPART;
+        mx = fmax(mx, P[0]);
+        for (int f = 0; f < 5; ++f) {
+            l2[f] += P[1 + f];
+            neumaier_add(s[f], c[f], P[6 + f]);
+            c[f] += P[11 + f];
+        }
+        bad += P[16];
+    }
+    out[0] = mx;
+    for (int f = 0; f < 5; ++f) {
+        out[1 + f] = sqrt(l2[f]);
+        out[6 + f] = s[f] + c[f];
+    }
+    out[11] = bad;
+}
+
+// ---------------------------------------------------------------------------
+// Debug point fields
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_debug_field(const JetDev<real> *__restrict__ jets, int jet,
+                                                       int field, double *out)
+{
+    const JetDev<real> &J = jets[jet];
+    const long long N = (long long)J.n[0] * J.n[1] * J.n[2];
+    for (long long lp = blockIdx.x * (long long)blockDim.x + threadIdx.x; lp < J.npts_pad;
+         lp += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        if (!point_of(J, lp, q)) continue;
+        long long dense = ((long long)q[2] * J.n[1] + q[1]) * J.n[0] + q[0];
+        const long long fs = J.fs;
+        switch (field) {
+        case LES_FIELD_MU_SGS: out[dense] = J.grad[G_MUSGS * fs + lp]; break;
+        case LES_FIELD_MU: out[dense] = J.prim[P_MU * fs + lp]; break;
+        case LES_FIELD_P: out[dense] = J.prim[P_P * fs + lp]; break;
+        case LES_FIELD_T: out[dense] = J.prim[P_T * fs + lp]; break;
+        case LES_FIELD_LAMBDA_XI: out[dense] = J.prim[P_LXI * fs + lp]; break;
+        case LES_FIELD_LAMBDA_ETA: out[dense] = J.prim[P_LETA * fs + lp]; break;
+        case LES_FIELD_LAMBDA_ZETA: out[dense] = J.prim[P_LZETA * fs + lp]; break;
+        case DBG_RHS:
+            for (int f = 0; f < NF; ++f) out[f * N + dense] = J.rhs[f * fs + lp];
+            break;
+        default:
+            if (field >= DBG_MET0 && field < DBG_MET0 + 9) out[dense] = J.met[(field - DBG_MET0) * fs + lp];
+            else if (field == DBG_MET0 + 9) out[dense] = J.jinv64[lp];
+            break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Surface probe: trilinear interpolation of rho, u, v, w, p
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_probe(const JetDev<real> *__restrict__ jets,
+                                                 const int *__restrict__ cell,
+                                                 const double *__restrict__ wts, int npts, int every,
+                                                 const long long *__restrict__ level_p,
+                                                 const long long *__restrict__ base_p, real *out,
+                                                 int capacity)
+{
+    const long long level = *level_p;
+    if (level % every != 0) return;
+    const long long frame = level / every - *base_p - 1;
+    if (frame < 0) return;
+    const JetDev<real> &J = jets[0];
+    const long long fs = J.fs;
+    real *o = out + (frame % capacity) * 5LL * npts;
+    const double g = J.gamma;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < npts; s += gridDim.x * blockDim.x) {
+        int lo[3] = {cell[3 * s], cell[3 * s + 1], cell[3 * s + 2]};
+        double t[3] = {wts[3 * s], wts[3 * s + 1], wts[3 * s + 2]};
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int c = 0; c < 8; ++c) {
+            int r[3];
+            double wgt = 1.0;
+            for (int a = 0; a < 3; ++a) {
+                int up = (c >> a) & 1;
+                r[a] = lo[a] + up;
+                wgt *= up ? t[a] : 1.0 - t[a];
+            }
+            long long p = lidx(J, r[0], r[1], r[2]);
+            double jinv = J.jinv64[p];
+            double Q[5];
+            for (int f = 0; f < 5; ++f) Q[f] = (double)J.q[0][f * fs + p] / jinv;
+            Prim64 pr = prim_of(Q, g);
+            acc[0] += wgt * pr.rho;
+            acc[1] += wgt * pr.u[0];
+            acc[2] += wgt * pr.u[1];
+            acc[3] += wgt * pr.u[2];
+            acc[4] += wgt * pr.p;
+        }
+        for (int f = 0; f < 5; ++f) o[(long long)f * npts + s] = (real)acc[f];
+    }
+}
+
+__global__ void k_step_advance(long long *level) { *level += 1; }
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+static int grid_for(long long work, int cap = 152 * 16)
+{
+    long long g = (work + BLOCK - 1) / BLOCK;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <typename real>
+void Launch<real>::metrics(const double *x, const double *y, const double *z, int ni, int nj, int nk,
+                           const int per[3], const double shift[9], double *met64, long long fs64,
+                           int pitch, double Cs, cudaStream_t st)
+{
+    CoordGrid G;
+    G.X[0] = x;
+    G.X[1] = y;
+    G.X[2] = z;
+    G.n[0] = ni;
+    G.n[1] = nj;
+    G.n[2] = nk;
+    for (int a = 0; a < 3; ++a) G.per[a] = per[a];
+    for (int t = 0; t < 9; ++t) G.shift[t] = shift[t];
+    k_metrics<<<grid_for((long long)ni * nj * nk), BLOCK, 0, st>>>(G, met64, fs64, pitch, Cs);
+}
+
+template <typename real>
+void Launch<real>::convert_metrics(const double *met64, long long fs64, real *met, long long fs,
+                                   long long npad, cudaStream_t st)
+{
+    k_convert_metrics<real><<<grid_for(npad), BLOCK, 0, st>>>(met64, fs64, met, fs, npad);
+}
+
+template <typename real>
+void Launch<real>::prims(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st)
+{
+    k_prims<real><<<grid, BLOCK, 0, st>>>(jets, bm, src);
+}
+
+template <typename real>
+void Launch<real>::grads(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st)
+{
+    k_grads<real><<<grid, BLOCK, 0, st>>>(jets, bm);
+}
+
+template <typename real>
+void Launch<real>::flux(const JetDev<real> *jets, BlockMap bm, int src, int dst, int stage,
+                        const double *dt, int rhs_only, int grid, cudaStream_t st)
+{
+    (void)src;
+    k_flux<real><<<grid, BLOCK, 0, st>>>(jets, bm, dst, stage, dt, rhs_only);
+}
+
+template <typename real>
+void Launch<real>::bc(const JetDev<real> *jets, BlockMap bm, int axis, int dst,
+                      const long long *level, int grid, cudaStream_t st)
+{
+    k_bc<real><<<grid, BLOCK, 0, st>>>(jets, bm, axis, dst, level);
+}
+
+template <typename real>
+void Launch<real>::set_state(const JetDev<real> *jets, int jet, const double *in, int kind,
+                             long long npad, cudaStream_t st)
+{
+    k_set_state<real><<<grid_for(npad), BLOCK, 0, st>>>(jets, jet, in, kind);
+}
+
+template <typename real>
+void Launch<real>::get_state(const JetDev<real> *jets, int jet, double *out, int kind,
+                             long long npad, cudaStream_t st)
+{
+    k_get_state<real><<<grid_for(npad), BLOCK, 0, st>>>(jets, jet, out, kind);
+}
+
+template <typename real>
+void Launch<real>::dt_max(const JetDev<real> *jets, BlockMap bm, unsigned long long *maxbits,
+                          int grid, cudaStream_t st)
+{
+    k_dt_max<real><<<grid, BLOCK, 0, st>>>(jets, bm, maxbits);
+}
+
+template <typename real>
+void Launch<real>::diag_partials(const JetDev<real> *jets, int jet, double *partials, int nblocks,
+                                 cudaStream_t st)
+{
+    k_diag_partials<real><<<nblocks, BLOCK, 0, st>>>(jets, jet, partials);
+}
+
+template <typename real>
+void Launch<real>::debug_field(const JetDev<real> *jets, int jet, int field, double *out,
+                               long long npad, cudaStream_t st)
+{
+    k_debug_field<real><<<grid_for(npad), BLOCK, 0, st>>>(jets, jet, field, out);
+}
+
+template <typename real>
+void Launch<real>::probe(const JetDev<real> *jets, const int *cell, const double *wts, int npts,
+                         int every, const long long *level, const long long *base, real *out,
+                         int capacity, cudaStream_t st)
+{
+    k_probe<real><<<grid_for(npts, 1024), BLOCK, 0, st>>>(jets, cell, wts, npts, every, level, base,
+                                                          out, capacity);
+}
+
+void launch_diag_final(const double *partials, int nblocks, double *out, cudaStream_t st)
+{
+    k_diag_final<<<1, 32, 0, st>>>(partials, nblocks, out);
+}
+
+void launch_step_advance(long long *level, cudaStream_t st) { k_step_advance<<<1, 1, 0, st>>>(level); }
+
+template struct Launch<float>;
+template struct Launch<double>;
+
+} // namespace les
