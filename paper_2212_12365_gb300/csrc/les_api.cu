@@ -497,11 +497,12 @@ static int bc_pass(les_handle *h, const BlockMap bcm[3], const JetDev<real> *jet
 
 // Optional per-launch event timing (les_profile_step); inactive during capture.
 struct Tracer {
-    cudaStream_t st = nullptr;
+    bool on = false;
+    cudaStream_t st = nullptr; // may be the legacy default stream (NULL)
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
     void begin(int kind)
     {
-        if (!st) return;
+        if (!on) return;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -510,7 +511,7 @@ struct Tracer {
     }
     void end()
     {
-        if (!st) return;
+        if (!on) return;
         cudaEventRecord(ev.back().second.second, st);
     }
 };
@@ -568,6 +569,7 @@ template <typename real> static int profile_impl(les_handle *h, int nsteps, doub
     }
     for (int s = 0; s < nsteps; ++s) {
         Tracer tr;
+        tr.on = true;
         tr.st = h->st;
         int rc = record_step<real>(h, h->st, &tr);
         CK(cudaStreamSynchronize(h->st));

@@ -89,6 +89,12 @@ __device__ double coord_at(const CoordGrid &G, int c, int q0, int q1, int q2)
     return G.X[c][((long long)q[2] * G.n[1] + q[1]) * G.n[0] + q[0]] + off;
 }
 
+// The metric stencils use explicitly rounded products and sums (no FMA
+// contraction): on a Cartesian-product grid the cross terms are then exact
+// zeros, as they are mathematically.  The boundary conditions branch on the
+// sign of the normal velocity, and an edge point whose interior neighbour
+// carries zero normal velocity must not see round-off residue there.
+
 // d x_c / d xi^a at lattice point q.
 __device__ double dcoord(const CoordGrid &G, int c, int a, const int q[3])
 {
@@ -98,7 +104,7 @@ __device__ double dcoord(const CoordGrid &G, int c, int a, const int q[3])
     for (int t = 0; t < s.n; ++t) {
         int r[3] = {q[0], q[1], q[2]};
         r[a] += s.off[t];
-        acc += s.wgt[t] * coord_at(G, c, r[0], r[1], r[2]);
+        acc = __dadd_rn(acc, __dmul_rn(s.wgt[t], coord_at(G, c, r[0], r[1], r[2])));
     }
     return acc;
 }
@@ -111,7 +117,8 @@ __device__ double dprod(const CoordGrid &G, int c1, int c2, int inner, int outer
     for (int t = 0; t < s.n; ++t) {
         int r[3] = {q[0], q[1], q[2]};
         r[outer] += s.off[t];
-        acc += s.wgt[t] * coord_at(G, c1, r[0], r[1], r[2]) * dcoord(G, c2, inner, r);
+        double prod = __dmul_rn(coord_at(G, c1, r[0], r[1], r[2]), dcoord(G, c2, inner, r));
+        acc = __dadd_rn(acc, __dmul_rn(s.wgt[t], prod));
     }
     return acc;
 }
@@ -133,16 +140,18 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
             int b = (a + 1) % 3, d = (a + 2) % 3;
             for (int c = 0; c < 3; ++c) {
                 int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-                met[(3 * a + c) * fs + o] = dprod(G, c1, c2, d, b, q) - dprod(G, c1, c2, b, d, q);
+                met[(3 * a + c) * fs + o] = __dsub_rn(dprod(G, c1, c2, d, b, q), dprod(G, c1, c2, b, d, q));
             }
         }
         double t[3][3];
         for (int c = 0; c < 3; ++c)
             for (int a = 0; a < 3; ++a) t[c][a] = dcoord(G, c, a, q);
         // determinant of d(x,y,z)/d(xi,eta,zeta), as printed for 1/J
-        double jinv = t[0][0] * (t[1][1] * t[2][2] - t[1][2] * t[2][1]) -
-                      t[0][1] * (t[1][0] * t[2][2] - t[1][2] * t[2][0]) +
-                      t[0][2] * (t[1][0] * t[2][1] - t[1][1] * t[2][0]);
+        double m0 = __dsub_rn(__dmul_rn(t[1][1], t[2][2]), __dmul_rn(t[1][2], t[2][1]));
+        double m1 = __dsub_rn(__dmul_rn(t[1][0], t[2][2]), __dmul_rn(t[1][2], t[2][0]));
+        double m2 = __dsub_rn(__dmul_rn(t[1][0], t[2][1]), __dmul_rn(t[1][1], t[2][0]));
+        double jinv = __dadd_rn(__dsub_rn(__dmul_rn(t[0][0], m0), __dmul_rn(t[0][1], m1)),
+                                __dmul_rn(t[0][2], m2));
         met[MET_JINV * fs + o] = jinv;
         double delta = cbrt(jinv); // filter width: cube root of the cell volume
         met[MET_CSD2 * fs + o] = (Cs * delta) * (Cs * delta);
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict_
             }
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const real *F = P + (P_U + f) * fs;
+                const real *F = P + (f < 3 ? P_U + f : P_T) * fs;
                 real acc = (real)s.wgt[0] * F[o[0]] + (real)s.wgt[1] * F[o[1]];
                 if (s.n == 3) acc += (real)s.wgt[2] * F[o[2]];
                 d[f][a] = acc;

@@ -125,7 +125,9 @@ def test_jet_small_10_steps_fp64():
     dor = oracle.diag(g, p, m, q10)
     assert d["max_abs_rhs_rho"] == pytest.approx(dor["max_abs_rhs_rho"], rel=1e-10)
     np.testing.assert_allclose(d["l2_rhs"], dor["l2_rhs"], rtol=1e-10)
-    np.testing.assert_allclose(d["sum_qhat"], dor["sum_qhat"], rtol=1e-13)
+    # sums of mostly cancelling terms: compare against the sum of magnitudes
+    mag = np.abs(q10).sum(axis=1)
+    assert np.all(np.abs(d["sum_qhat"] - dor["sum_qhat"]) <= 1e-13 * mag)
     s.close()
 
 
