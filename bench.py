@@ -41,6 +41,7 @@ WORKLOADS = {
     "jet-384x256x144": (I.jet_paper_scale, "fp64"),
     "jet-768x384x192": (I.jet_large, "fp32"),
     "jet-48x32x32": (I.jet_small, "fp64"),
+    "jet-192x128x72": (I.jet_medium, "fp64"),
 }
 
 

@@ -209,6 +209,32 @@ int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts)
 /* Kernel launches issued by the most recent les_step call (all steps). */
 int64_t les_last_launch_count(les_handle *h);
 
+/* Residual / conservation sums without any device allocation.  The paper
+ * has no counterpart: this is a library service for callers that must not
+ * allocate device memory — code inside a framework whose caching allocator
+ * holds (nearly) all device memory, and per-step monitoring hooks that
+ * cannot afford cudaMalloc/cudaFree latency or their device-wide
+ * synchronisation.  It computes what les_get_diagnostics reports from the
+ * caller's own buffers:
+ *   qhat, rhs : device arrays of 5*npoints doubles, [field][point] (dense
+ *               layout of les_get_state LES_STATE_RAW and les_debug_rhs);
+ *               rhs should be zero at boundary points;
+ *   out       : device array of 12 doubles: [0] max |rhs_rho|,
+ *               [1..5] sqrt(sum rhs_f^2), [6..10] compensated sum of qhat_f,
+ *               [11] count of non-finite values;
+ *   stream    : cudaStream_t the two kernels are launched on (NULL allowed).
+ * Asynchronous; allocates nothing.  Its scratch is one file-scope device
+ * array of LES_NOALLOC_MAX_POINTS/65536 x 17 doubles (557 KB), held by every
+ * GPU that loads the library until exit; the first call on a device looks up
+ * that array's device address (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU (different streams without
+ * ordering) race and give wrong sums.  Errors: LES_ERR_ARG for null pointers,
+ * npoints < 1 or npoints > LES_NOALLOC_MAX_POINTS (with a message on stderr),
+ * LES_ERR_CUDA if the address lookup or a launch fails. */
+#define LES_NOALLOC_MAX_POINTS 268435456LL
+int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints, double *out,
+                          void *stream);
+
 const char *les_last_error(les_handle *h);
 int les_destroy(les_handle *h);
 

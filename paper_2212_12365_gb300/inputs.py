@@ -117,6 +117,15 @@ def jet_paper_scale() -> tuple[GridSpec, FlowParams]:
             FlowParams(mach_j=1.4, TR=1.0, Re=1.0e5, Cs=0.17, cfl=0.5, seed=2))
 
 
+def jet_medium() -> tuple[GridSpec, FlowParams]:
+    """192x128x72 jet (~1.77M points): the paper-scale jet at half resolution
+    per axis, for profiling captures (state + metrics still far above L2)."""
+    hy = 0.4 * 12.0 / 127
+    hz = 0.4 * 12.0 / 71
+    return (jet_grid(192, 128, 72, 30.0, 12.0, 12.0, hy, hz),
+            FlowParams(mach_j=1.4, TR=1.0, Re=1.0e5, Cs=0.17, cfl=0.5, seed=3))
+
+
 def jet_large() -> tuple[GridSpec, FlowParams]:
     """768x384x192 jet (~56.6M points), 30D x 12D x 12D, TR 2."""
     hy = 0.4 * 12.0 / 383

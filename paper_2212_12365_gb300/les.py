@@ -32,7 +32,7 @@ EXPORTED = [
     "les_set_state_jet", "les_step", "les_get_state", "les_get_state_jet", "les_set_time",
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
-    "les_last_launch_count",
+    "les_last_launch_count", "les_diag_sums_noalloc",
     "les_last_error", "les_destroy",
 ]
 
@@ -95,6 +95,7 @@ def lib():
         L.les_profile_step.argtypes = [vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]
         L.les_last_launch_count.argtypes = [vp]
         L.les_last_launch_count.restype = ctypes.c_int64
+        L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.les_last_error.argtypes = [vp]
         L.les_last_error.restype = ctypes.c_char_p
         L.les_destroy.argtypes = [vp]
@@ -261,6 +262,16 @@ def les_profile_step(h, nsteps: int):
 
 def les_last_launch_count(h) -> int:
     return int(lib().les_last_launch_count(h))
+
+
+NOALLOC_MAX_POINTS = 268435456
+
+
+def les_diag_sums_noalloc(qhat_ptr: int, rhs_ptr: int, npoints: int, out_ptr: int, stream=None) -> int:
+    """Device-pointer form; returns the library's status code."""
+    return int(lib().les_diag_sums_noalloc(ctypes.c_void_p(qhat_ptr), ctypes.c_void_p(rhs_ptr),
+                                           int(npoints), ctypes.c_void_p(out_ptr),
+                                           stream if stream is not None else current_stream()))
 
 
 def les_destroy(h):
