@@ -198,12 +198,13 @@ int les_debug_field(les_handle *h, int jet, int field, double *out);
  * device time per kernel kind into ms_out[LES_KERNEL_KINDS] (milliseconds,
  * summed over launches) and the launch counts into counts (may be NULL).
  * The state advances exactly as with les_step.  Synchronises the stream. */
-#define LES_KERNEL_PRIMS 0  /* primitives, Sutherland, lambda-bar */
-#define LES_KERNEL_GRADS 1  /* derivatives, Smagorinsky mu_sgs */
-#define LES_KERNEL_FLUX 2   /* interface fluxes, residual, stage update */
-#define LES_KERNEL_BC 3     /* boundary faces */
-#define LES_KERNEL_OTHER 4  /* time-level counter, probe */
-#define LES_KERNEL_KINDS 5
+#define LES_KERNEL_POINT 0  /* primitives, Sutherland, lambda-bar, point fluxes */
+#define LES_KERNEL_GRADS 1  /* derivatives, Smagorinsky/Eidson, pressure sensor */
+#define LES_KERNEL_IFACE 2  /* interface fluxes (inviscid, dissipation, viscous) */
+#define LES_KERNEL_UPDATE 3 /* flux differences and stage update */
+#define LES_KERNEL_BC 4     /* boundary faces */
+#define LES_KERNEL_OTHER 5  /* time-level counter, probe */
+#define LES_KERNEL_KINDS 6
 int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts);
 
 /* Kernel launches issued by the most recent les_step call (all steps). */

@@ -29,7 +29,7 @@ struct JetHost {
     size_t off;                        // byte offset of this jet's region
     size_t bytes;                      // size of this jet's region
     // device pointers (typed as bytes; the element type follows the precision)
-    char *met, *q[3], *prim, *grad, *rhs;
+    char *met, *q[3], *prim, *grad, *hflux, *rhs;
     double *jinv64, *inflow_r;
     int nblk_pt, nblk_bc[3];
 };
@@ -148,6 +148,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     size_t o_q2 = take(NF * fb);
     size_t o_prim = take(NPRIM * fb);
     size_t o_grad = take(NGRAD * fb);
+    size_t o_hf = take(NHF * fb);
     size_t o_rhs = take(NF * fb);
     size_t o_inr = take((size_t)g->nj * g->nk * 8);
     J.bytes = off;
@@ -159,6 +160,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     J.q[2] = (char *)o_q2;
     J.prim = (char *)o_prim;
     J.grad = (char *)o_grad;
+    J.hflux = (char *)o_hf;
     J.rhs = (char *)o_rhs;
     J.inflow_r = (double *)o_inr;
 }
@@ -221,6 +223,7 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.jinv64 = J.jinv64;
     D.prim = (real *)J.prim;
     D.grad = (real *)J.grad;
+    D.hflux = (real *)J.hflux;
     D.rhs = (real *)J.rhs;
     D.inflow_r = J.inflow_r;
     const les_params &p = J.prm;
@@ -235,6 +238,9 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.k2 = p.k2;
     D.k4 = p.k4;
     D.suth_S = p.S1_dim / (p.TR * p.T_inf_dim);
+    D.inv_Re = 1.0 / p.Re;
+    D.kap_mol = 1.0 / (p.Re * p.Pr * (p.gamma - 1.0));
+    D.kap_sgs = 1.0 / (p.Pr_sgs * (p.gamma - 1.0));
     D.seed = (unsigned long long)p.seed;
     (void)h;
 }
@@ -255,6 +261,8 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
         met64 = (double *)align_up((size_t)(tmp + 3 * N), 256);
     Launch<real>::metrics(dx, dy, dz, J.n[0], J.n[1], J.n[2], J.per, J.shift, met64, J.fs, J.pitch,
                           J.prm.Cs, h->st);
+    CK(cudaGetLastError());
+    Launch<real>::static_fields(met64, J.fs, J.pitch, J.n, J.per, h->st);
     CK(cudaGetLastError());
     if (h->prec == LES_FP32) {
         Launch<real>::convert_metrics(met64, J.fs, (real *)J.met, J.fs, J.npad, h->st);
@@ -377,6 +385,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
         for (int s = 0; s < 3; ++s) J.q[s] = jb + (size_t)J.q[s];
         J.prim = jb + (size_t)J.prim;
         J.grad = jb + (size_t)J.grad;
+        J.hflux = jb + (size_t)J.hflux;
         J.rhs = jb + (size_t)J.rhs;
         J.inflow_r = (double *)(jb + (size_t)J.inflow_r);
     }
@@ -473,9 +482,10 @@ static int rhs_pass(les_handle *h, const BlockMap &pt, const JetDev<real> *jets,
                     int rhs_only, int dst, int stage)
 {
     int gp = grid_cap(h, pt.total);
-    Launch<real>::prims(jets, pt, src, gp, h->st);
+    Launch<real>::point(jets, pt, src, gp, h->st);
     Launch<real>::grads(jets, pt, gp, h->st);
-    Launch<real>::flux(jets, pt, src, dst, stage, h->d_dt, rhs_only, gp, h->st);
+    Launch<real>::iface(jets, pt, gp, h->st);
+    Launch<real>::update(jets, pt, dst, stage, h->d_dt, rhs_only, gp, h->st);
     CK(cudaGetLastError());
     return LES_OK;
 }
@@ -531,16 +541,19 @@ template <typename real> static int record_step(les_handle *h, cudaStream_t st, 
     h->launches_per_step++;
     int gp = grid_cap(h, h->pt.total);
     for (int s = 0; s < 5; ++s) {
-        T.begin(LES_KERNEL_PRIMS);
-        Launch<real>::prims(jets, h->pt, src_of[s], gp, st);
+        T.begin(LES_KERNEL_POINT);
+        Launch<real>::point(jets, h->pt, src_of[s], gp, st);
         T.end();
         T.begin(LES_KERNEL_GRADS);
         Launch<real>::grads(jets, h->pt, gp, st);
         T.end();
-        T.begin(LES_KERNEL_FLUX);
-        Launch<real>::flux(jets, h->pt, src_of[s], dst_of[s], s, h->d_dt, 0, gp, st);
+        T.begin(LES_KERNEL_IFACE);
+        Launch<real>::iface(jets, h->pt, gp, st);
         T.end();
-        h->launches_per_step += 3;
+        T.begin(LES_KERNEL_UPDATE);
+        Launch<real>::update(jets, h->pt, dst_of[s], s, h->d_dt, 0, gp, st);
+        T.end();
+        h->launches_per_step += 4;
         for (int oi = 0; oi < 3; ++oi) {
             int a = order[oi];
             if (h->bcm[a].total == 0) continue;
@@ -654,7 +667,7 @@ template <typename real> static int set_state_impl(les_handle *h, int jet, const
     if (rc) return rc;
     if (h->dt[jet] == 0.0) {
         BlockMap p1 = h->pt1[jet];
-        Launch<real>::prims(one, p1, 0, grid_cap(h, p1.total), h->st);
+        Launch<real>::point(one, p1, 0, grid_cap(h, p1.total), h->st);
         CK(cudaMemsetAsync(h->d_dtbits + jet, 0, 8, h->st));
         Launch<real>::dt_max(one, p1, h->d_dtbits + jet, grid_cap(h, p1.total), h->st);
         CK(cudaGetLastError());
@@ -801,13 +814,13 @@ extern "C" int les_debug_field(les_handle *h, int jet, int field, double *out)
     if (h->prec == LES_FP64) {
         const JetDev<double> *one = (const JetDev<double> *)h->d_jets + jet;
         int gp = grid_cap(h, h->pt1[jet].total);
-        Launch<double>::prims(one, h->pt1[jet], 0, gp, h->st);
+        Launch<double>::point(one, h->pt1[jet], 0, gp, h->st);
         Launch<double>::grads(one, h->pt1[jet], gp, h->st);
         rc = export_impl<double>(h, jet, field, out, N);
     } else {
         const JetDev<float> *one = (const JetDev<float> *)h->d_jets + jet;
         int gp = grid_cap(h, h->pt1[jet].total);
-        Launch<float>::prims(one, h->pt1[jet], 0, gp, h->st);
+        Launch<float>::point(one, h->pt1[jet], 0, gp, h->st);
         Launch<float>::grads(one, h->pt1[jet], gp, h->st);
         rc = export_impl<float>(h, jet, field, out, N);
     }

@@ -14,13 +14,34 @@
 namespace les {
 
 constexpr int NF = 5;         // conserved variables
-constexpr int NMET = 11;      // J^-1 xi_x .. J^-1 zeta_z (9), J^-1, (Cs Delta)^2
+// Static per-point grid fields (computed once in FP64, stored in the state
+// precision): the nine metric cofactors J^-1 d xi^a / d x_c at [3a + c],
+// J^-1, (Cs Delta)^2, J, and per axis a: the J^-1 average of the interface
+// to the +a neighbour, its reciprocal, and |row a| = sqrt(sum_c m_ac^2).
+constexpr int NMET = 21;
 constexpr int MET_JINV = 9;
 constexpr int MET_CSD2 = 10;
-constexpr int NPRIM = 10;     // rho u v w p T mu lbar_xi lbar_eta lbar_zeta
-enum { P_RHO = 0, P_U, P_V, P_W, P_P, P_T, P_MU, P_LXI, P_LETA, P_LZETA };
-constexpr int NGRAD = 13;     // d(u,v,w,T)/d(xi,eta,zeta) as [phi*3 + axis], mu_sgs
+constexpr int MET_J = 11;
+constexpr int MET_JB = 12;    // + a
+constexpr int MET_RJB = 15;   // + a
+constexpr int MET_NORM = 18;  // + a
+// Per-point stage fields: primitives, Sutherland viscosity, lambda-bar,
+// the unscaled conserved vector W0..W3 (= rho is P_RHO) and rho H = e + p,
+// and the inviscid point fluxes F_a (5 each) at P_F0 + 5a + f.
+constexpr int NPRIM = 29;
+enum {
+    P_RHO = 0, P_U, P_V, P_W, P_P, P_T, P_MU, P_LXI, P_LETA, P_LZETA,
+    P_RU, P_RV, P_RW, P_RH, P_F0
+};
+// Per-point derivative fields: d(u,v,w,T)/d(xi,eta,zeta) at [3*phi + axis],
+// mu_sgs, mu/Re + mu_sgs, the total conductivity, and the pressure sensor
+// per axis.
+constexpr int NGRAD = 18;
 constexpr int G_MUSGS = 12;
+constexpr int G_MUEFF = 13;
+constexpr int G_KAP = 14;
+constexpr int G_NU = 15;      // + a
+constexpr int NHF = 15;       // interface fluxes H_a at [5a + f], interface L + e_a/2
 
 constexpr int BLOCK = 256;    // threads per block of the point / face kernels
 constexpr int DBG_RHS = 100;  // debug export codes beside the LES_FIELD_* values
@@ -41,10 +62,14 @@ struct JetDev {
     const double *jinv64; // J^-1 in FP64 (conversions of the state)
     real *prim;        // NPRIM fields (scratch, rebuilt every stage)
     real *grad;        // NGRAD fields (scratch)
+    real *hflux;       // NHF fields (scratch): interface fluxes
     real *rhs;         // NF fields (residual for diagnostics / debug)
     const double *inflow_r; // nj*nk: radius sqrt(y^2+z^2) of the i = 0 face points
     // flow parameters (jet units)
     double gamma, Pr, Pr_sgs, Re, mach, TR, theta, noise_amp, k2, k4, suth_S;
+    double inv_Re;     // 1/Re (0 for an inviscid run)
+    double kap_mol;    // mu -> conductivity: 1/(Re Pr (gamma-1))
+    double kap_sgs;    // mu_sgs -> conductivity: 1/(Pr_sgs (gamma-1))
     unsigned long long seed;
     long long npts_pad; // nk*nj*pitch
 };
@@ -79,17 +104,79 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n)
     return a < 0 ? a + n : a;
 }
 
-// Kernel launchers (les_kernels.cu), all asynchronous on `st`.
+#ifdef __CUDACC__
+// Unit stencil of a second-order first derivative along one axis with
+// Delta xi = 1: central, or one-sided 3-point at the ends of a non-periodic
+// axis.  off[] are index offsets, wgt[] the weights.
+struct Stencil {
+    int n;
+    int off[3];
+    double wgt[3];
+};
+
+__device__ __forceinline__ Stencil deriv_stencil(int q, int n, int periodic)
+{
+    Stencil s;
+    if (periodic || (q > 0 && q < n - 1)) {
+        s.n = 2;
+        s.off[0] = -1; s.wgt[0] = -0.5;
+        s.off[1] = 1;  s.wgt[1] = 0.5;
+        s.off[2] = 0;  s.wgt[2] = 0.0;
+    } else if (q == 0) {
+        s.n = 3;
+        s.off[0] = 0; s.wgt[0] = -1.5;
+        s.off[1] = 1; s.wgt[1] = 2.0;
+        s.off[2] = 2; s.wgt[2] = -0.5;
+    } else {
+        s.n = 3;
+        s.off[0] = 0;  s.wgt[0] = 1.5;
+        s.off[1] = -1; s.wgt[1] = -2.0;
+        s.off[2] = -2; s.wgt[2] = 0.5;
+    }
+    return s;
+}
+
+// Point (i,j,k) of padded linear index lp; false for padding columns.
+
+template <typename real>
+__device__ __forceinline__ bool point_of(const JetDev<real> &J, long long lp, int q[3])
+{
+    int i = (int)(lp % J.pitch);
+    long long r = lp / J.pitch;
+    q[0] = i;
+    q[1] = (int)(r % J.n[1]);
+    q[2] = (int)(r / J.n[1]);
+    return i < J.n[0] && q[2] < J.n[2];
+}
+
+template <typename real>
+__device__ __forceinline__ bool is_end(const JetDev<real> &J, int a, int qa)
+{
+    return !J.per[a] && (qa == 0 || qa == J.n[a] - 1);
+}
+
+template <typename real>
+__device__ __forceinline__ bool interior(const JetDev<real> &J, const int q[3])
+{
+    return !(is_end(J, 0, q[0]) || is_end(J, 1, q[1]) || is_end(J, 2, q[2]));
+}
+
+#endif
+
+// Kernel launchers (les_kernels.cu, les_stage.cu), all asynchronous on `st`.
 template <typename real> struct Launch {
     static void metrics(const double *x, const double *y, const double *z, int ni, int nj, int nk,
                         const int per[3], const double shift[9], double *met64, long long fs64,
                         int pitch, double Cs, cudaStream_t st);
     static void convert_metrics(const double *met64, long long fs64, real *met, long long fs,
                                 long long npad, cudaStream_t st);
-    static void prims(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st);
+    static void static_fields(double *met64, long long fs64, int pitch, const int n[3],
+                              const int per[3], cudaStream_t st);
+    static void point(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st);
     static void grads(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st);
-    static void flux(const JetDev<real> *jets, BlockMap bm, int src, int dst, int stage,
-                     const double *dt, int rhs_only, int grid, cudaStream_t st);
+    static void iface(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st);
+    static void update(const JetDev<real> *jets, BlockMap bm, int dst, int stage,
+                       const double *dt, int rhs_only, int grid, cudaStream_t st);
     static void bc(const JetDev<real> *jets, BlockMap bm, int axis, int dst,
                    const long long *level, int grid, cudaStream_t st);
     static void set_state(const JetDev<real> *jets, int jet, const double *in, int kind,

@@ -1,18 +1,13 @@
 // CUDA kernels of libles.so (sm_103a).
 //
-// One Runge-Kutta stage (Sec. "Time Marching Method", Eq. localdt) runs as
-//   k_prims  : per point, primitives (Sec. LES formulation: EOS, Sutherland),
-//              spectral-radius scaling lambda-bar (Sec. Numerical Formulation)
-//   k_grads  : per point, computational velocity/temperature derivatives and
-//              the Smagorinsky eddy viscosity (Sec. Subgrid Scale Modeling)
-//   k_flux   : per interior point, the six interface fluxes (centred inviscid
-//              flux, Turkel-Vatsa dissipation, compact viscous + SGS flux),
-//              their differences (Eq. spatial_discret) and the stage update
-//   k_bc     : boundary faces of one axis (Sec. Boundary Conditions); launched
-//              for y, then z, then x
-// All kernels are persistent grid-stride loops over a block map that spans one
-// or many jets (batched form); the per-point arithmetic does not depend on the
-// map, so a jet gives the same bits alone or in a batch.
+// Grid setup (metrics and static fields), boundary conditions, state
+// conversion, time step, diagnostics, debug export and probe kernels.  The
+// Runge-Kutta stage kernels are in les_stage.cu.
+//   k_bc : boundary faces of one axis (Sec. "Boundary Conditions"); launched
+//          for y, then z, then x after every stage
+// All per-point kernels are persistent grid-stride loops over a block map that
+// spans one or many jets (batched form); the per-point arithmetic does not
+// depend on the map, so a jet gives the same bits alone or in a batch.
 #include <cmath>
 #include <cstdint>
 
@@ -23,37 +18,6 @@ namespace les {
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
-
-// Unit stencil of a second-order first derivative along one axis with
-// Delta xi = 1: central, or one-sided 3-point at the ends of a non-periodic
-// axis.  off[] are index offsets, wgt[] the weights.
-struct Stencil {
-    int n;
-    int off[3];
-    double wgt[3];
-};
-
-__device__ __forceinline__ Stencil deriv_stencil(int q, int n, int periodic)
-{
-    Stencil s;
-    if (periodic || (q > 0 && q < n - 1)) {
-        s.n = 2;
-        s.off[0] = -1; s.wgt[0] = -0.5;
-        s.off[1] = 1;  s.wgt[1] = 0.5;
-        s.off[2] = 0;  s.wgt[2] = 0.0;
-    } else if (q == 0) {
-        s.n = 3;
-        s.off[0] = 0; s.wgt[0] = -1.5;
-        s.off[1] = 1; s.wgt[1] = 2.0;
-        s.off[2] = 2; s.wgt[2] = -0.5;
-    } else {
-        s.n = 3;
-        s.off[0] = 0;  s.wgt[0] = 1.5;
-        s.off[1] = -1; s.wgt[1] = -2.0;
-        s.off[2] = -2; s.wgt[2] = 0.5;
-    }
-    return s;
-}
 
 __device__ __forceinline__ int floordiv_i(int a, int n)
 {
@@ -158,6 +122,39 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
     }
 }
 
+// Static per-point fields derived from the metrics (FP64): J = 1/J^-1; per
+// axis a the interface average of J^-1 towards the +a neighbour, its
+// reciprocal, and the norm of metric row a.
+__global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long fs, int pitch, int ni,
+                                                         int nj, int nk, int p0, int p1, int p2)
+{
+    const int n[3] = {ni, nj, nk};
+    const int per[3] = {p0, p1, p2};
+    const long long total = (long long)ni * nj * nk;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        int q[3];
+        q[0] = (int)(p % ni);
+        q[1] = (int)((p / ni) % nj);
+        q[2] = (int)(p / ((long long)ni * nj));
+        const long long o = ((long long)q[2] * nj + q[1]) * pitch + q[0];
+        const double jinv = met[MET_JINV * fs + o];
+        met[MET_J * fs + o] = 1.0 / jinv;
+        for (int a = 0; a < 3; ++a) {
+            int r[3] = {q[0], q[1], q[2]};
+            if (per[a]) r[a] = (q[a] + 1) % n[a];
+            else if (q[a] + 1 < n[a]) r[a] = q[a] + 1;
+            const long long oR = ((long long)r[2] * nj + r[1]) * pitch + r[0];
+            const double jb = 0.5 * (jinv + met[MET_JINV * fs + oR]);
+            met[(MET_JB + a) * fs + o] = jb;
+            met[(MET_RJB + a) * fs + o] = 1.0 / jb;
+            const double mx = met[(3 * a) * fs + o], my = met[(3 * a + 1) * fs + o],
+                         mz = met[(3 * a + 2) * fs + o];
+            met[(MET_NORM + a) * fs + o] = sqrt(mx * mx + my * my + mz * mz);
+        }
+    }
+}
+
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_convert_metrics(const double *met64, long long fs64,
                                                            real *met, long long fs, long long npad)
@@ -165,351 +162,6 @@ __global__ void __launch_bounds__(BLOCK) k_convert_metrics(const double *met64, 
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npad;
          p += (long long)gridDim.x * blockDim.x)
         for (int f = 0; f < NMET; ++f) met[f * fs + p] = (real)met64[f * fs64 + p];
-}
-
-// ---------------------------------------------------------------------------
-// Point decomposition of a virtual block
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__device__ __forceinline__ bool point_of(const JetDev<real> &J, long long lp, int q[3])
-{
-    int i = (int)(lp % J.pitch);
-    long long r = lp / J.pitch;
-    q[0] = i;
-    q[1] = (int)(r % J.n[1]);
-    q[2] = (int)(r / J.n[1]);
-    return i < J.n[0] && q[2] < J.n[2];
-}
-
-template <typename real>
-__device__ __forceinline__ bool is_end(const JetDev<real> &J, int a, int qa)
-{
-    return !J.per[a] && (qa == 0 || qa == J.n[a] - 1);
-}
-
-template <typename real>
-__device__ __forceinline__ bool interior(const JetDev<real> &J, const int q[3])
-{
-    return !(is_end(J, 0, q[0]) || is_end(J, 1, q[1]) || is_end(J, 2, q[2]));
-}
-
-// ---------------------------------------------------------------------------
-// k_prims: primitives, Sutherland viscosity, lambda-bar
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_prims(const JetDev<real> *__restrict__ jets, BlockMap bm,
-                                                 int src)
-{
-    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
-        int jet = find_jet(bm, vb);
-        const JetDev<real> &J = jets[jet];
-        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
-        if (lp >= J.npts_pad) continue;
-        int q[3];
-        if (!point_of(J, lp, q)) continue;
-        const real *Q = J.q[src];
-        const long long fs = J.fs;
-        const real gam = (real)J.gamma;
-        real jinv = J.met[MET_JINV * fs + lp];
-        real rj = real(1) / jinv;
-        real q0 = Q[lp];
-        real rq0 = real(1) / q0;
-        real rho = q0 * rj;
-        real u = Q[fs + lp] * rq0, v = Q[2 * fs + lp] * rq0, w = Q[3 * fs + lp] * rq0;
-        real e = Q[4 * fs + lp] * rj;
-        real p = (gam - real(1)) * (e - real(0.5) * rho * (u * u + v * v + w * w));
-        real T = gam * p / rho;
-        real S = (real)J.suth_S;
-        real mu = T * sqrt(T) * (real(1) + S) / (T + S);
-        real c = sqrt(T); // c^2 = gamma p / rho = T in jet units
-        real lam[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            real mx = J.met[(3 * a) * fs + lp], my = J.met[(3 * a + 1) * fs + lp],
-                 mz = J.met[(3 * a + 2) * fs + lp];
-            real U = (mx * u + my * v + mz * w) * rj;
-            lam[a] = fabs(U) + c * sqrt(mx * mx + my * my + mz * mz) * rj;
-        }
-        real s01 = sqrt(lam[0] * lam[1]), s02 = sqrt(lam[0] * lam[2]), s12 = sqrt(lam[1] * lam[2]);
-        real *P = J.prim;
-        P[P_RHO * fs + lp] = rho;
-        P[P_U * fs + lp] = u;
-        P[P_V * fs + lp] = v;
-        P[P_W * fs + lp] = w;
-        P[P_P * fs + lp] = p;
-        P[P_T * fs + lp] = T;
-        P[P_MU * fs + lp] = mu;
-        // lambda-bar_a = lambda_a [1 + (lambda_b/lambda_a)^1/2 + (lambda_d/lambda_a)^1/2]
-        P[P_LXI * fs + lp] = lam[0] + s01 + s02;
-        P[P_LETA * fs + lp] = lam[1] + s01 + s12;
-        P[P_LZETA * fs + lp] = lam[2] + s02 + s12;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_grads: computational derivatives of u, v, w, T and mu_sgs
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict__ jets, BlockMap bm)
-{
-    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
-        int jet = find_jet(bm, vb);
-        const JetDev<real> &J = jets[jet];
-        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
-        if (lp >= J.npts_pad) continue;
-        int q[3];
-        if (!point_of(J, lp, q)) continue;
-        const long long fs = J.fs;
-        const real *P = J.prim;
-        real d[4][3]; // d phi / d xi^a for phi = u, v, w, T
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            Stencil s = deriv_stencil(q[a], J.n[a], J.per[a]);
-            long long o[3];
-            for (int t = 0; t < 3; ++t) {
-                int r[3] = {q[0], q[1], q[2]};
-                r[a] = J.per[a] ? wrapi(r[a] + s.off[t], J.n[a]) : r[a] + s.off[t];
-                o[t] = lidx(J, r[0], r[1], r[2]);
-            }
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const real *F = P + (f < 3 ? P_U + f : P_T) * fs;
-                real acc = (real)s.wgt[0] * F[o[0]] + (real)s.wgt[1] * F[o[1]];
-                if (s.n == 3) acc += (real)s.wgt[2] * F[o[2]];
-                d[f][a] = acc;
-            }
-        }
-        real *G = J.grad;
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) G[(3 * f + a) * fs + lp] = d[f][a];
-        // velocity gradient d u_i / d x_c = J (sum_a (J^-1 d xi^a/d x_c) d u_i / d xi^a)
-        real m[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) m[t] = J.met[t * fs + lp];
-        real rj = real(1) / J.met[MET_JINV * fs + lp];
-        real gu[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                gu[i][c] = (m[c] * d[i][0] + m[3 + c] * d[i][1] + m[6 + c] * d[i][2]) * rj;
-        real ss = real(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                real sic = real(0.5) * (gu[i][c] + gu[c][i]);
-                ss += sic * sic;
-            }
-        // Smagorinsky: mu_sgs = rho (Cs Delta)^2 (2 S_ij S_ij)^1/2
-        G[G_MUSGS * fs + lp] = P[P_RHO * fs + lp] * J.met[MET_CSD2 * fs + lp] * sqrt(real(2) * ss);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Interface flux (Eq. inv_flux_vec with Eq. dissip_term, minus the viscous
-// flux of Eqs. hat-flux-Ev/Fv/Gv) between point L and L + e_a.
-// ---------------------------------------------------------------------------
-
-template <typename real>
-__device__ __noinline__ void interface_flux(const JetDev<real> &J, int a, int iL0, int iL1, int iL2,
-                                            real *H)
-{
-    const long long fs = J.fs;
-    const real *P = J.prim;
-    const real *G = J.grad;
-    const real *M = J.met;
-    int qL[3] = {iL0, iL1, iL2};
-    int qR[3] = {iL0, iL1, iL2};
-    qR[a] = J.per[a] ? wrapi(qL[a] + 1, J.n[a]) : qL[a] + 1;
-    const long long L = lidx(J, qL[0], qL[1], qL[2]);
-    const long long R = lidx(J, qR[0], qR[1], qR[2]);
-    const bool lo_end = !J.per[a] && qL[a] == 0;
-    const bool hi_end = !J.per[a] && qR[a] == J.n[a] - 1;
-    long long Lm = L, Rp = R;
-    if (!lo_end) {
-        int r[3] = {qL[0], qL[1], qL[2]};
-        r[a] = J.per[a] ? wrapi(qL[a] - 1, J.n[a]) : qL[a] - 1;
-        Lm = lidx(J, r[0], r[1], r[2]);
-    }
-    if (!hi_end) {
-        int r[3] = {qR[0], qR[1], qR[2]};
-        r[a] = J.per[a] ? wrapi(qR[a] + 1, J.n[a]) : qR[a] + 1;
-        Rp = lidx(J, r[0], r[1], r[2]);
-    }
-    const real gam = (real)J.gamma;
-    const real gm1 = gam - real(1);
-    const real hgam = gam / gm1;
-
-    // primitive values of the (up to) four points along the axis
-    real rho[4], u[4], v[4], w[4], p[4];
-    const long long idx4[4] = {Lm, L, R, Rp};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        long long o = idx4[t];
-        rho[t] = P[P_RHO * fs + o];
-        u[t] = P[P_U * fs + o];
-        v[t] = P[P_V * fs + o];
-        w[t] = P[P_W * fs + o];
-        p[t] = P[P_P * fs + o];
-    }
-    // dissipation vector W = [rho, rho u, rho v, rho w, e + p] (unscaled)
-    real W[4][5];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        W[t][0] = rho[t];
-        W[t][1] = rho[t] * u[t];
-        W[t][2] = rho[t] * v[t];
-        W[t][3] = rho[t] * w[t];
-        W[t][4] = hgam * p[t] + real(0.5) * rho[t] * (u[t] * u[t] + v[t] * v[t] + w[t] * w[t]);
-    }
-    // pressure sensors of L and R; an end point takes its interior neighbour's
-    real nuL, nuR;
-    {
-        real sL = fabs(p[2] - real(2) * p[1] + p[0]) / (p[2] + real(2) * p[1] + p[0]);
-        real sR = fabs(p[3] - real(2) * p[2] + p[1]) / (p[3] + real(2) * p[2] + p[1]);
-        nuL = lo_end ? sR : sL;
-        nuR = hi_end ? sL : sR;
-    }
-    const real eps2 = (real)J.k2 * fmax(nuL, nuR);
-    const real eps4 = fmax(real(0), (real)J.k4 - eps2);
-    const real lamL = P[(P_LXI + a) * fs + L], lamR = P[(P_LXI + a) * fs + R];
-    const real lam = real(0.5) * (lamL + lamR);
-    const real jinvL = M[MET_JINV * fs + L], jinvR = M[MET_JINV * fs + R];
-    const real jb = real(0.5) * (jinvL + jinvR);
-
-    // metric rows of L and R
-    real mL[9], mR[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        mL[t] = M[t * fs + L];
-        mR[t] = M[t * fs + R];
-    }
-    // centred inviscid flux 0.5 (F_L + F_R); J^-1 U = m_a . u
-    real Fc[5];
-    {
-        const real *ma = mL + 3 * a;
-        const real *mb = mR + 3 * a;
-        real JUL = ma[0] * u[1] + ma[1] * v[1] + ma[2] * w[1];
-        real JUR = mb[0] * u[2] + mb[1] * v[2] + mb[2] * w[2];
-        Fc[0] = real(0.5) * (rho[1] * JUL + rho[2] * JUR);
-        Fc[1] = real(0.5) * (W[1][1] * JUL + p[1] * ma[0] + W[2][1] * JUR + p[2] * mb[0]);
-        Fc[2] = real(0.5) * (W[1][2] * JUL + p[1] * ma[1] + W[2][2] * JUR + p[2] * mb[1]);
-        Fc[3] = real(0.5) * (W[1][3] * JUL + p[1] * ma[2] + W[2][3] * JUR + p[2] * mb[2]);
-        Fc[4] = real(0.5) * (W[1][4] * JUL + W[2][4] * JUR);
-    }
-    // Turkel-Vatsa dissipation with the boundary extrapolation of dW
-    real Dis[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-        real dW0 = W[2][f] - W[1][f];
-        real dWp = hi_end ? -dW0 : W[3][f] - W[2][f];
-        real dWm = lo_end ? -dW0 : W[1][f] - W[0][f];
-        real d3 = dWp - real(2) * dW0 + dWm;
-        Dis[f] = jb * lam * (eps2 * dW0 - eps4 * d3);
-    }
-    // compact viscous + SGS flux
-    real Fv[5];
-    {
-        real dphi[4][3];
-        real phiL[4] = {u[1], v[1], w[1], P[P_T * fs + L]};
-        real phiR[4] = {u[2], v[2], w[2], P[P_T * fs + R]};
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                dphi[f][b] = (b == a) ? phiR[f] - phiL[f]
-                                      : real(0.5) * (G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R]);
-        real mc[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) mc[t] = real(0.5) * (mL[t] + mR[t]);
-        real rjb = real(1) / jb;
-        real gu[4][3];
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                gu[f][c] = (mc[c] * dphi[f][0] + mc[3 + c] * dphi[f][1] + mc[6 + c] * dphi[f][2]) * rjb;
-        real div = gu[0][0] + gu[1][1] + gu[2][2];
-        real mu = real(0.5) * (P[P_MU * fs + L] + P[P_MU * fs + R]);
-        real mus = real(0.5) * (G[G_MUSGS * fs + L] + G[G_MUSGS * fs + R]);
-        real mure = mu / (real)J.Re;
-        real coef = real(2) * (mure + mus);
-        real tau[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                real s = real(0.5) * (gu[i][c] + gu[c][i]);
-                tau[i][c] = coef * (i == c ? s - div / real(3) : s);
-            }
-        real kap = mure / (gm1 * (real)J.Pr) + mus / (gm1 * (real)J.Pr_sgs);
-        real vb[3] = {real(0.5) * (u[1] + u[2]), real(0.5) * (v[1] + v[2]), real(0.5) * (w[1] + w[2])};
-        real beta[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            beta[i] = tau[i][0] * vb[0] + tau[i][1] * vb[1] + tau[i][2] * vb[2] + kap * gu[3][i];
-        const real *mr = mc + 3 * a;
-        Fv[0] = real(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) Fv[1 + i] = mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
-        Fv[4] = mr[0] * beta[0] + mr[1] * beta[1] + mr[2] * beta[2];
-    }
-#pragma unroll
-    for (int f = 0; f < 5; ++f) H[f] = Fc[f] - Dis[f] - Fv[f];
-}
-
-__constant__ double c_rk_alpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
-
-// Stage update Q(dst) = Q(0) - alpha_stage dt RHS(prims of Q(src)), or (rhs_only)
-// RHS into J.rhs with zeros at boundary points.
-template <typename real>
-__global__ void __launch_bounds__(BLOCK) k_flux(const JetDev<real> *__restrict__ jets, BlockMap bm,
-                                                int dst, int stage, const double *__restrict__ dt,
-                                                int rhs_only)
-{
-    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
-        int jet = find_jet(bm, vb);
-        const JetDev<real> &J = jets[jet];
-        long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
-        if (lp >= J.npts_pad) continue;
-        int q[3];
-        if (!point_of(J, lp, q)) continue;
-        const long long fs = J.fs;
-        if (!interior(J, q)) {
-            if (rhs_only)
-                for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = real(0);
-            continue;
-        }
-        real R[5] = {0, 0, 0, 0, 0};
-        for (int a = 0; a < 3; ++a) {
-#pragma unroll 1
-            for (int s = 0; s < 2; ++s) {
-                int r[3] = {q[0], q[1], q[2]};
-                if (s == 0) r[a] = J.per[a] ? wrapi(q[a] - 1, J.n[a]) : q[a] - 1;
-                real H[5];
-                interface_flux<real>(J, a, r[0], r[1], r[2], H);
-                real sg = s == 0 ? real(-1) : real(1);
-#pragma unroll
-                for (int f = 0; f < 5; ++f) R[f] += sg * H[f];
-            }
-        }
-        if (rhs_only) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = R[f];
-        } else {
-            real adt = (real)(c_rk_alpha[stage] * dt[jet]);
-            const real *Q0 = J.q[0];
-            real *Qd = J.q[dst];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) Qd[f * fs + lp] = Q0[f * fs + lp] - adt * R[f];
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -986,30 +638,18 @@ void Launch<real>::metrics(const double *x, const double *y, const double *z, in
 }
 
 template <typename real>
+void Launch<real>::static_fields(double *met64, long long fs64, int pitch, const int n[3],
+                                 const int per[3], cudaStream_t st)
+{
+    k_static_fields<<<grid_for((long long)n[0] * n[1] * n[2]), BLOCK, 0, st>>>(
+        met64, fs64, pitch, n[0], n[1], n[2], per[0], per[1], per[2]);
+}
+
+template <typename real>
 void Launch<real>::convert_metrics(const double *met64, long long fs64, real *met, long long fs,
                                    long long npad, cudaStream_t st)
 {
     k_convert_metrics<real><<<grid_for(npad), BLOCK, 0, st>>>(met64, fs64, met, fs, npad);
-}
-
-template <typename real>
-void Launch<real>::prims(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st)
-{
-    k_prims<real><<<grid, BLOCK, 0, st>>>(jets, bm, src);
-}
-
-template <typename real>
-void Launch<real>::grads(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st)
-{
-    k_grads<real><<<grid, BLOCK, 0, st>>>(jets, bm);
-}
-
-template <typename real>
-void Launch<real>::flux(const JetDev<real> *jets, BlockMap bm, int src, int dst, int stage,
-                        const double *dt, int rhs_only, int grid, cudaStream_t st)
-{
-    (void)src;
-    k_flux<real><<<grid, BLOCK, 0, st>>>(jets, bm, dst, stage, dt, rhs_only);
 }
 
 template <typename real>

@@ -1,0 +1,396 @@
+// Runge-Kutta stage kernels (Sec. "Time Marching Method", Eq. localdt) of
+// libles.so.  One stage runs as four persistent grid-stride kernels:
+//   k_point  : per point — primitives from Qhat (EOS, Sec. "Large Eddy
+//              Simulation Formulation"), Sutherland mu(T), spectral radii and
+//              the anisotropic scaling lambda-bar (Sec. "Numerical
+//              Formulation"), the dissipation vector W = Q + [0,0,0,0,p] and
+//              the inviscid point fluxes E_e, F_e, G_e (Eq. hat-flux-G)
+//   k_grads  : per point — second-order derivatives of u, v, w, T along the
+//              three grid axes, the Smagorinsky eddy viscosity and Eidson
+//              conductivity (Sec. "Subgrid Scale Modeling"), the pressure
+//              sensor per axis (Eq. p_grad_sensor)
+//   k_iface  : per interface (one thread owns the +1/2 interfaces of its
+//              point along the three axes) — centred inviscid flux minus the
+//              Turkel-Vatsa dissipation J^-1 d (Eqs. inv_flux_vec,
+//              dissip_term, eps_2/4_dissip) minus the compact viscous + SGS
+//              flux (Eqs. hat-flux-Ev/Fv/Gv)
+//   k_update : per interior point — the flux differences (Eq. for RHS with
+//              Delta xi = 1) and Q(l) = Q(0) - alpha_l dt RHS
+// Each interface flux is evaluated once, so the residual of a periodic
+// direction telescopes exactly.  On GB300 the FP64 form is bound by the FP64
+// pipe, not by HBM: the intermediate fields cost bandwidth that is otherwise
+// idle and remove recomputation (divisions, square roots) from the hot loop.
+#include <cmath>
+
+#include "les_internal.cuh"
+
+namespace les {
+
+__constant__ double c_alpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
+
+// ---------------------------------------------------------------------------
+// k_point
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                                 int src)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        const int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        const long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        int q[3];
+        if (lp >= J.npts_pad || !point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        const real *__restrict__ Q = J.q[src];
+        const real *__restrict__ M = J.met;
+        real *__restrict__ P = J.prim;
+        const real gam = (real)J.gamma;
+        const real rj = M[MET_J * fs + lp];
+        const real rho = Q[lp] * rj;
+        const real ru = Q[fs + lp] * rj, rv = Q[2 * fs + lp] * rj, rw = Q[3 * fs + lp] * rj;
+        const real e = Q[4 * fs + lp] * rj;
+        const real rrho = real(1) / rho;
+        const real u = ru * rrho, v = rv * rrho, w = rw * rrho;
+        const real p = (gam - real(1)) * (e - real(0.5) * (ru * u + rv * v + rw * w));
+        const real T = gam * p * rrho;
+        const real sT = sqrt(T); // speed of sound: c^2 = gamma p / rho = T in jet units
+        const real S = (real)J.suth_S;
+        const real mu = T * sT * (real(1) + S) / (T + S);
+        const real rH = e + p;
+        real lam[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const real mx = M[(3 * a) * fs + lp], my = M[(3 * a + 1) * fs + lp],
+                       mz = M[(3 * a + 2) * fs + lp];
+            const real JU = mx * u + my * v + mz * w; // J^-1 times the contravariant velocity
+            lam[a] = (fabs(JU) + sT * M[(MET_NORM + a) * fs + lp]) * rj;
+            real *F = P + (P_F0 + 5 * a) * fs + lp;
+            F[0] = rho * JU;
+            F[fs] = ru * JU + p * mx;
+            F[2 * fs] = rv * JU + p * my;
+            F[3 * fs] = rw * JU + p * mz;
+            F[4 * fs] = rH * JU;
+        }
+        const real s01 = sqrt(lam[0] * lam[1]), s02 = sqrt(lam[0] * lam[2]),
+                   s12 = sqrt(lam[1] * lam[2]);
+        P[P_RHO * fs + lp] = rho;
+        P[P_U * fs + lp] = u;
+        P[P_V * fs + lp] = v;
+        P[P_W * fs + lp] = w;
+        P[P_P * fs + lp] = p;
+        P[P_T * fs + lp] = T;
+        P[P_MU * fs + lp] = mu;
+        // lambda-bar_a = lambda_a [1 + (lambda_b/lambda_a)^1/2 + (lambda_d/lambda_a)^1/2]
+        P[P_LXI * fs + lp] = lam[0] + s01 + s02;
+        P[P_LETA * fs + lp] = lam[1] + s01 + s12;
+        P[P_LZETA * fs + lp] = lam[2] + s02 + s12;
+        P[P_RU * fs + lp] = ru;
+        P[P_RV * fs + lp] = rv;
+        P[P_RW * fs + lp] = rw;
+        P[P_RH * fs + lp] = rH;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_grads
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict__ jets, BlockMap bm)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        const int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        const long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        int q[3];
+        if (lp >= J.npts_pad || !point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        const real *__restrict__ P = J.prim;
+        const real *__restrict__ M = J.met;
+        real *__restrict__ G = J.grad;
+        real d[4][3]; // d phi / d xi^a, phi = u, v, w, T
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const Stencil s = deriv_stencil(q[a], J.n[a], J.per[a]);
+            long long o[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                int r[3] = {q[0], q[1], q[2]};
+                r[a] = J.per[a] ? wrapi(r[a] + s.off[t], J.n[a]) : r[a] + s.off[t];
+                o[t] = lidx(J, r[0], r[1], r[2]);
+            }
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const real *F = P + (f < 3 ? P_U + f : P_T) * fs;
+                real acc = (real)s.wgt[0] * F[o[0]] + (real)s.wgt[1] * F[o[1]];
+                if (s.n == 3) acc += (real)s.wgt[2] * F[o[2]];
+                d[f][a] = acc;
+            }
+            // pressure sensor along a; an end point of a non-periodic axis
+            // takes the sensor of its interior neighbour
+            int c = q[a];
+            if (!J.per[a]) c = c < 1 ? 1 : (c > J.n[a] - 2 ? J.n[a] - 2 : c);
+            int rm[3] = {q[0], q[1], q[2]}, r0[3] = {q[0], q[1], q[2]}, rp[3] = {q[0], q[1], q[2]};
+            r0[a] = c;
+            rm[a] = J.per[a] ? wrapi(c - 1, J.n[a]) : c - 1;
+            rp[a] = J.per[a] ? wrapi(c + 1, J.n[a]) : c + 1;
+            const real pm = P[P_P * fs + lidx(J, rm[0], rm[1], rm[2])];
+            const real p0 = P[P_P * fs + lidx(J, r0[0], r0[1], r0[2])];
+            const real pp = P[P_P * fs + lidx(J, rp[0], rp[1], rp[2])];
+            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) / (pp + real(2) * p0 + pm);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) G[(3 * f + a) * fs + lp] = d[f][a];
+        real m[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) m[t] = M[t * fs + lp];
+        const real rj = M[MET_J * fs + lp];
+        real gu[3][3]; // d u_i / d x_c (chain rule through the metric cofactors)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gu[i][c] = (m[c] * d[i][0] + m[3 + c] * d[i][1] + m[6 + c] * d[i][2]) * rj;
+        real ss = real(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ss += gu[i][i] * gu[i][i];
+#pragma unroll
+            for (int c = i + 1; c < 3; ++c) {
+                const real sic = real(0.5) * (gu[i][c] + gu[c][i]);
+                ss += real(2) * sic * sic;
+            }
+        }
+        // Smagorinsky: mu_sgs = rho (Cs Delta)^2 (2 S_ij S_ij)^1/2
+        const real mus = P[P_RHO * fs + lp] * M[MET_CSD2 * fs + lp] * sqrt(real(2) * ss);
+        const real mu = P[P_MU * fs + lp];
+        G[G_MUSGS * fs + lp] = mus;
+        G[G_MUEFF * fs + lp] = mu * (real)J.inv_Re + mus;
+        // Eidson: k_sgs = mu_sgs Cp / Pr_sgs; molecular k = mu Cp / (Re Pr), Cp = 1/(gamma-1)
+        G[G_KAP * fs + lp] = mu * (real)J.kap_mol + mus * (real)J.kap_sgs;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_iface: flux through the interface between L and R = L + e_a
+// ---------------------------------------------------------------------------
+
+// The axis is a template parameter so that every metric/derivative index is a
+// compile-time constant (no local-memory arrays).
+template <typename real, int a>
+__device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3], long long L,
+                                           real *__restrict__ H)
+{
+    const long long fs = J.fs;
+    const real *__restrict__ P = J.prim;
+    const real *__restrict__ G = J.grad;
+    const real *__restrict__ M = J.met;
+    int qR[3] = {qL[0], qL[1], qL[2]};
+    qR[a] = J.per[a] ? wrapi(qL[a] + 1, J.n[a]) : qL[a] + 1;
+    const long long R = lidx(J, qR[0], qR[1], qR[2]);
+    const bool lo_end = !J.per[a] && qL[a] == 0;
+    const bool hi_end = !J.per[a] && qR[a] == J.n[a] - 1;
+    long long Lm = L, Rp = R;
+    if (!lo_end) {
+        int r[3] = {qL[0], qL[1], qL[2]};
+        r[a] = J.per[a] ? wrapi(qL[a] - 1, J.n[a]) : qL[a] - 1;
+        Lm = lidx(J, r[0], r[1], r[2]);
+    }
+    if (!hi_end) {
+        int r[3] = {qR[0], qR[1], qR[2]};
+        r[a] = J.per[a] ? wrapi(qR[a] + 1, J.n[a]) : qR[a] + 1;
+        Rp = lidx(J, r[0], r[1], r[2]);
+    }
+    // Turkel-Vatsa: eps2 = k2 max(nu_L, nu_R), eps4 = max(0, k4 - eps2),
+    // scaled by the interface lambda-bar and J^-1
+    const real eps2 = (real)J.k2 * fmax(G[(G_NU + a) * fs + L], G[(G_NU + a) * fs + R]);
+    const real eps4 = fmax(real(0), (real)J.k4 - eps2);
+    const real jb = M[(MET_JB + a) * fs + L];
+    const real sc = jb * real(0.5) * (P[(P_LXI + a) * fs + L] + P[(P_LXI + a) * fs + R]);
+    const real se2 = sc * eps2, se4 = sc * eps4;
+    const int wf[5] = {P_RHO, P_RU, P_RV, P_RW, P_RH};
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const real *W = P + wf[f] * fs;
+        const real wL = W[L], wR = W[R];
+        const real dW0 = wR - wL;
+        const real dWp = hi_end ? -dW0 : W[Rp] - wR;
+        const real dWm = lo_end ? -dW0 : wL - W[Lm];
+        const real d3 = dWp - real(2) * dW0 + dWm;
+        const real *F = P + (P_F0 + 5 * a + f) * fs;
+        H[f] = real(0.5) * (F[L] + F[R]) - (se2 * dW0 - se4 * d3);
+    }
+    // compact viscous + SGS flux: normal derivative from the two points,
+    // tangential derivatives averaged, coefficients/metrics/velocity averaged
+    real dphi[4][3];
+    const int pf[4] = {P_U, P_V, P_W, P_T};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            dphi[f][b] = (b == a) ? P[pf[f] * fs + R] - P[pf[f] * fs + L]
+                                  : real(0.5) * (G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R]);
+    real mc[9];
+    const real rjb = M[(MET_RJB + a) * fs + L];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) mc[t] = real(0.5) * (M[t * fs + L] + M[t * fs + R]);
+    real gu[4][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            gu[f][c] = (mc[c] * dphi[f][0] + mc[3 + c] * dphi[f][1] + mc[6 + c] * dphi[f][2]) * rjb;
+    const real div3 = (gu[0][0] + gu[1][1] + gu[2][2]) * real(1.0 / 3.0);
+    const real coef = G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]; // 2 x average
+    const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]);
+    real tau[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        tau[i][i] = coef * (gu[i][i] - div3);
+#pragma unroll
+        for (int c = i + 1; c < 3; ++c) {
+            tau[i][c] = coef * real(0.5) * (gu[i][c] + gu[c][i]);
+            tau[c][i] = tau[i][c];
+        }
+    }
+    const real vb[3] = {real(0.5) * (P[P_U * fs + L] + P[P_U * fs + R]),
+                        real(0.5) * (P[P_V * fs + L] + P[P_V * fs + R]),
+                        real(0.5) * (P[P_W * fs + L] + P[P_W * fs + R])};
+    const real *mr = mc + 3 * a;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) H[1 + i] -= mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
+    real fe = real(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // beta_c = tau_cj u_j - q_c with q = -k grad T
+        const real beta = tau[c][0] * vb[0] + tau[c][1] * vb[1] + tau[c][2] * vb[2] + kap * gu[3][c];
+        fe += mr[c] * beta;
+    }
+    H[4] -= fe;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_iface(const JetDev<real> *__restrict__ jets, BlockMap bm)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        const int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        const long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        int q[3];
+        if (lp >= J.npts_pad || !point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        real H[5];
+        // no interface beyond the last point of a non-periodic axis
+        if (J.per[0] || q[0] < J.n[0] - 1) {
+            iface_flux<real, 0>(J, q, lp, H);
+#pragma unroll
+            for (int f = 0; f < 5; ++f) J.hflux[f * fs + lp] = H[f];
+        }
+        if (J.per[1] || q[1] < J.n[1] - 1) {
+            iface_flux<real, 1>(J, q, lp, H);
+#pragma unroll
+            for (int f = 0; f < 5; ++f) J.hflux[(5 + f) * fs + lp] = H[f];
+        }
+        if (J.per[2] || q[2] < J.n[2] - 1) {
+            iface_flux<real, 2>(J, q, lp, H);
+#pragma unroll
+            for (int f = 0; f < 5; ++f) J.hflux[(10 + f) * fs + lp] = H[f];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_update: RHS = sum_a H_a(P) - H_a(P - e_a); Q(dst) = Q(0) - alpha dt RHS
+// ---------------------------------------------------------------------------
+
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_update(const JetDev<real> *__restrict__ jets, BlockMap bm,
+                                                  int dst, int stage, const double *__restrict__ dt,
+                                                  int rhs_only)
+{
+    for (int vb = blockIdx.x; vb < bm.total; vb += gridDim.x) {
+        const int jet = find_jet(bm, vb);
+        const JetDev<real> &J = jets[jet];
+        const long long lp = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
+        int q[3];
+        if (lp >= J.npts_pad || !point_of(J, lp, q)) continue;
+        const long long fs = J.fs;
+        if (!interior(J, q)) {
+            if (rhs_only)
+                for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = real(0);
+            continue;
+        }
+        long long back[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int r[3] = {q[0], q[1], q[2]};
+            r[a] = J.per[a] ? wrapi(q[a] - 1, J.n[a]) : q[a] - 1;
+            back[a] = lidx(J, r[0], r[1], r[2]);
+        }
+        const real *__restrict__ Hf = J.hflux;
+        real R[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            real acc = real(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc += Hf[(5 * a + f) * fs + lp] - Hf[(5 * a + f) * fs + back[a]];
+            R[f] = acc;
+        }
+        if (rhs_only) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) J.rhs[f * fs + lp] = R[f];
+        } else {
+            const real adt = (real)(c_alpha[stage] * dt[jet]);
+            const real *Q0 = J.q[0];
+            real *Qd = J.q[dst];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) Qd[f * fs + lp] = Q0[f * fs + lp] - adt * R[f];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+template <typename real>
+void Launch<real>::point(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st)
+{
+    k_point<real><<<grid, BLOCK, 0, st>>>(jets, bm, src);
+}
+
+template <typename real>
+void Launch<real>::grads(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st)
+{
+    k_grads<real><<<grid, BLOCK, 0, st>>>(jets, bm);
+}
+
+template <typename real>
+void Launch<real>::iface(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st)
+{
+    k_iface<real><<<grid, BLOCK, 0, st>>>(jets, bm);
+}
+
+template <typename real>
+void Launch<real>::update(const JetDev<real> *jets, BlockMap bm, int dst, int stage, const double *dt,
+                          int rhs_only, int grid, cudaStream_t st)
+{
+    k_update<real><<<grid, BLOCK, 0, st>>>(jets, bm, dst, stage, dt, rhs_only);
+}
+
+template void Launch<float>::point(const JetDev<float> *, BlockMap, int, int, cudaStream_t);
+template void Launch<double>::point(const JetDev<double> *, BlockMap, int, int, cudaStream_t);
+template void Launch<float>::grads(const JetDev<float> *, BlockMap, int, cudaStream_t);
+template void Launch<double>::grads(const JetDev<double> *, BlockMap, int, cudaStream_t);
+template void Launch<float>::iface(const JetDev<float> *, BlockMap, int, cudaStream_t);
+template void Launch<double>::iface(const JetDev<double> *, BlockMap, int, cudaStream_t);
+template void Launch<float>::update(const JetDev<float> *, BlockMap, int, int, const double *, int, int,
+                                    cudaStream_t);
+template void Launch<double>::update(const JetDev<double> *, BlockMap, int, int, const double *, int, int,
+                                     cudaStream_t);
+
+} // namespace les

@@ -248,7 +248,7 @@ def les_probe_frames(h) -> int:
     return f.value
 
 
-KERNEL_KINDS = ("prims", "grads", "flux", "bc", "other")
+KERNEL_KINDS = ("point", "grads", "iface", "update", "bc", "other")
 
 
 def les_profile_step(h, nsteps: int):
