@@ -234,7 +234,8 @@ def run_ours(args):
                 "traffic": None,
                 "peak_source": f"nominal {'FP64' if prec == 'fp64' else 'FP32'} unit count x 2.07 GHz",
                 "share": prof[dom][0] / tot if tot else None,
-                "per_kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items()},
+                "per_kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+                "stage": les.les_describe(solver.h),
                 "hbm_gbs_measured_peak": peaks.get("hbm_gbs")}
 
     # end to end through the public API: pinned host state in, step, state out

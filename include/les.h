@@ -236,6 +236,12 @@ int64_t les_last_launch_count(les_handle *h);
 int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints, double *out,
                           void *stream);
 
+/* Human-readable description of a handle: precision, jets, device bytes and
+ * the stage kernel configuration chosen by the autotuner (FP32: fused tile
+ * height and k-chunk; FP64: four-kernel stage).  Valid until the next call
+ * on the handle. */
+const char *les_describe(les_handle *h);
+
 const char *les_last_error(les_handle *h);
 int les_destroy(les_handle *h);
 

@@ -2,6 +2,7 @@
 // state transfer, diagnostics and the surface probe behind the C ABI of les.h.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -67,6 +68,13 @@ struct les_handle {
     std::vector<double> dt;
     std::vector<char> has_state;
     cudaGraphExec_t gexec = nullptr;
+    // fused FP32 stage: work-list tables (all jets; and one per jet with item0 = 0)
+    FusedJet *d_fj = nullptr, *d_fj1 = nullptr;
+    std::vector<FusedJet> fj;
+    int fused_ty = 16;
+    int fused_items = 0;
+    bool tuned = false;
+    std::string tune_note;
     int64_t launches_per_step = 0;
     int64_t last_launches = 0;
     // probe
@@ -166,7 +174,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
 }
 
 struct GlobalPlan {
-    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, total;
+    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, total;
 };
 
 static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, long long maxN)
@@ -187,6 +195,7 @@ static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, lon
     P.o_diag = take(sizeof(double) * 16);
     P.o_pbase = take(sizeof(long long));
     P.o_stage = take(sizeof(double) * 5 * (size_t)maxN);
+    P.o_fj = take(sizeof(FusedJet) * 2 * njets);
     P.total = off;
     return P;
 }
@@ -307,6 +316,52 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
     return LES_OK;
 }
 
+// Interior output range length of one axis.
+static int out_len(const JetHost &J, int a) { return J.per[a] ? J.n[a] : J.n[a] - 2; }
+
+// Work-list tables of the fused stage for tile height ty and k-chunk kc.
+static int set_fused_tiling(les_handle *h, int ty, int kc)
+{
+    int acc = 0;
+    std::vector<FusedJet> one(h->njets);
+    for (int j = 0; j < h->njets; ++j) {
+        FusedJet &F = h->fj[j];
+        const JetHost &J = h->J[j];
+        F.nbx = (out_len(J, 0) + 29) / 30;
+        F.nby = (out_len(J, 1) + ty - 3) / (ty - 2);
+        F.kc = std::max(1, std::min(kc, out_len(J, 2)));
+        F.nkc = (out_len(J, 2) + F.kc - 1) / F.kc;
+        F.item0 = acc;
+        acc += F.nbx * F.nby * F.nkc;
+        one[j] = F;
+        one[j].item0 = 0;
+    }
+    h->fused_ty = ty;
+    h->fused_items = acc;
+    CK(cudaMemcpyAsync(h->d_fj, h->fj.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->d_fj1, one.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LES_OK;
+}
+
+static int items_of(const FusedJet &F) { return F.nbx * F.nby * F.nkc; }
+static int autotune_fused(les_handle *h);
+
+// One fused stage (or residual) over all jets (jet < 0) or one jet.
+static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, int rhs_only, cudaStream_t st)
+{
+    const JetDev<float> *jets = (const JetDev<float> *)h->d_jets;
+    const FusedJet *fj = jet < 0 ? h->d_fj : h->d_fj1 + jet;
+    const int nj = jet < 0 ? h->njets : 1;
+    const int items = jet < 0 ? h->fused_items : items_of(h->fj[jet]);
+    const int grid = std::max(1, std::min(items, h->nsm * (h->fused_ty == 16 ? 1 : 2)));
+    if (jet >= 0) jets += jet;
+    if (h->fused_ty == 16)
+        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, st);
+    else
+        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, st);
+}
+
 template <typename real>
 static int create_impl(const les_grid_desc *g, const les_params *p, int njets, void *stream,
                        les_handle **out)
@@ -377,6 +432,8 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     h->d_diag = (double *)(B + GP.o_diag);
     h->d_probe_base = (long long *)(B + GP.o_pbase);
     h->d_stage = (double *)(B + GP.o_stage);
+    h->d_fj = (FusedJet *)(B + GP.o_fj);
+    h->d_fj1 = h->d_fj + njets;
     for (int j = 0; j < njets; ++j) {
         JetHost &J = h->J[j];
         char *jb = B + gbytes + J.off;
@@ -397,6 +454,28 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     std::vector<JetDev<real>> D(njets);
     for (int j = 0; j < njets; ++j) fill_jetdev<real>(h, h->J[j], D[j]);
     CK(cudaMemcpyAsync(h->d_jets, D.data(), sizeof(JetDev<real>) * njets, cudaMemcpyHostToDevice, h->st));
+    if (h->prec == LES_FP32) {
+        if (fused_prepare<16>() != 0 || fused_prepare<8>() != 0)
+            return bail(fail(h, LES_ERR_CUDA, "fused kernel shared-memory attribute"));
+        h->fj.resize(njets);
+        for (int j = 0; j < njets; ++j) {
+            FusedParams &F = h->fj[j].fp;
+            const les_params &pp = h->J[j].prm;
+            F.gam = (float)pp.gamma;
+            F.gm1 = (float)(pp.gamma - 1.0);
+            F.hgam = (float)(pp.gamma / (pp.gamma - 1.0));
+            F.k2 = (float)pp.k2;
+            F.k4 = (float)pp.k4;
+            F.inv_Re = (float)(1.0 / pp.Re);
+            F.kap_mol = (float)(1.0 / (pp.Re * pp.Pr * (pp.gamma - 1.0)));
+            F.kap_sgs = (float)(1.0 / (pp.Pr_sgs * (pp.gamma - 1.0)));
+            const double S = pp.S1_dim / (pp.TR * pp.T_inf_dim);
+            F.suth1 = (float)(1.0 + S);
+            F.suthS = (float)S;
+        }
+        int rc = set_fused_tiling(h, 8, 32);
+        if (rc) return bail(rc);
+    }
     // block maps: [pt | bc0 | bc1 | bc2] each njets+1, then per-jet pairs
     std::vector<int> maps(4 * (njets + 1) + 8 * njets);
     for (int fam = 0; fam < 4; ++fam) {
@@ -541,6 +620,22 @@ template <typename real> static int record_step(les_handle *h, cudaStream_t st, 
     h->launches_per_step++;
     int gp = grid_cap(h, h->pt.total);
     for (int s = 0; s < 5; ++s) {
+        if (h->prec == LES_FP32) {
+            // fused single-pass stage: counted as the interface kernel kind
+            T.begin(LES_KERNEL_IFACE);
+            fused_launch(h, -1, src_of[s], dst_of[s], s, 0, st);
+            T.end();
+            h->launches_per_step += 1;
+            for (int oi = 0; oi < 3; ++oi) {
+                int a = order[oi];
+                if (h->bcm[a].total == 0) continue;
+                T.begin(LES_KERNEL_BC);
+                Launch<real>::bc(jets, h->bcm[a], a, dst_of[s], h->d_level, grid_cap(h, h->bcm[a].total), st);
+                T.end();
+                h->launches_per_step++;
+            }
+            continue;
+        }
         T.begin(LES_KERNEL_POINT);
         Launch<real>::point(jets, h->pt, src_of[s], gp, st);
         T.end();
@@ -605,6 +700,11 @@ extern "C" int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64
     if (!h || nsteps < 0 || !ms_out) return LES_ERR_ARG;
     for (int j = 0; j < h->njets; ++j)
         if (!h->has_state[j]) return fail(h, LES_ERR_STATE, "les_profile_step before les_set_state");
+    if (h->prec == LES_FP32 && !h->tuned) {
+        int rc = autotune_fused(h);
+        if (rc) return rc;
+        h->tuned = true;
+    }
     return h->prec == LES_FP64 ? profile_impl<double>(h, nsteps, ms_out, counts)
                                : profile_impl<float>(h, nsteps, ms_out, counts);
 }
@@ -635,6 +735,11 @@ extern "C" int les_step(les_handle *h, int nsteps)
     if (!h || nsteps < 0) return LES_ERR_ARG;
     for (int j = 0; j < h->njets; ++j)
         if (!h->has_state[j]) return fail(h, LES_ERR_STATE, "les_step before les_set_state");
+    if (h->prec == LES_FP32 && !h->tuned) {
+        int rc = autotune_fused(h);
+        if (rc) return rc;
+        h->tuned = true;
+    }
     if (!h->gexec) {
         int rc = h->prec == LES_FP64 ? capture_step<double>(h) : capture_step<float>(h);
         if (rc) return rc;
@@ -739,8 +844,61 @@ extern "C" int les_get_time(les_handle *h, int64_t *step, double *dt)
 
 template <typename real> static int residual_of_jet(les_handle *h, int jet)
 {
+    if (h->prec == LES_FP32) {
+        // the same fused kernel as the steps; it writes interior points only
+        JetHost &J = h->J[jet];
+        CK(cudaMemsetAsync(J.rhs, 0, (size_t)J.fs * NF * sizeof(float), h->st));
+        fused_launch(h, jet, 0, 0, 0, 1, h->st);
+        CK(cudaGetLastError());
+        return LES_OK;
+    }
     const JetDev<real> *one = (const JetDev<real> *)h->d_jets + jet;
     return rhs_pass<real>(h, h->pt1[jet], one, 0, 1, 0, 0);
+}
+
+// Autotuner of the fused stage: time (tile height, k-chunk) candidates with
+// residual launches on the current state and keep the fastest; the choice is
+// cached per set of grid shapes for the process.
+static std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+static int autotune_fused(les_handle *h)
+{
+    std::string key;
+    for (auto &J : h->J)
+        key += std::to_string(J.n[0]) + "x" + std::to_string(J.n[1]) + "x" + std::to_string(J.n[2]) + "p" +
+               std::to_string(J.per[0] * 4 + J.per[1] * 2 + J.per[2]) + ";";
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end()) {
+        const int tys[2] = {16, 8};
+        const int kcs[6] = {8, 16, 24, 48, 96, 100000};
+        float best = 1e30f;
+        std::pair<int, int> pick{8, 48};
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int ty : tys)
+            for (int kc : kcs) {
+                int rc = set_fused_tiling(h, ty, kc);
+                if (rc) return rc;
+                fused_launch(h, -1, 0, 0, 0, 1, h->st); // warm-up
+                CK(cudaEventRecord(e0, h->st));
+                fused_launch(h, -1, 0, 0, 0, 1, h->st);
+                fused_launch(h, -1, 0, 0, 0, 1, h->st);
+                CK(cudaEventRecord(e1, h->st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    pick = {ty, kc};
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        it = g_tune_cache.emplace(key, pick).first;
+    }
+    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" + std::to_string(it->second.second);
+    return set_fused_tiling(h, it->second.first, it->second.second);
 }
 
 template <typename real> static int diag_impl(les_handle *h, int jet, les_diag *d)
@@ -896,6 +1054,18 @@ extern "C" int les_probe_frames(les_handle *h, int64_t *frames)
 extern "C" int64_t les_last_launch_count(les_handle *h) { return h ? h->last_launches : 0; }
 
 extern "C" const char *les_last_error(les_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" const char *les_describe(les_handle *h)
+{
+    if (!h) return "null handle";
+    static thread_local std::string d;
+    d = std::string(h->prec == LES_FP64 ? "fp64" : "fp32") + " jets=" + std::to_string(h->njets) +
+        " device_bytes=" + std::to_string(h->bytes) + " stage=" +
+        (h->prec == LES_FP64 ? std::string("point+grads+iface+update")
+                             : std::string("fused ") + (h->tuned ? h->tune_note : "ty=" + std::to_string(h->fused_ty) + " (untuned)")) +
+        " launches_per_step=" + std::to_string(h->launches_per_step);
+    return d.c_str();
+}
 
 extern "C" int les_destroy(les_handle *h)
 {

@@ -163,6 +163,29 @@ __device__ __forceinline__ bool interior(const JetDev<real> &J, const int q[3])
 
 #endif
 
+// Flow constants of one jet in FP32 for the fused stage kernel.
+struct FusedParams {
+    float gam, gm1, hgam;   // gamma, gamma - 1, gamma / (gamma - 1)
+    float k2, k4;           // Turkel-Vatsa constants
+    float inv_Re, kap_mol, kap_sgs;
+    float suth1, suthS;     // Sutherland: mu = T^1.5 suth1 / (T + suthS)
+};
+
+// Work-list entry of one jet for the fused stage kernel: items
+// [item0, item0 + nbx*nby*nkc) are its (tile x, tile y, k-chunk) triples.
+struct FusedJet {
+    int item0;
+    int nbx, nby, nkc;
+    int kc;                 // planes per k-chunk
+    FusedParams fp;
+};
+
+template <int TY> size_t fused_smem_bytes();
+template <int TY> int fused_prepare();
+template <int TY>
+void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
+                  int src, int dst, int stage, const double *dt, int rhs_only, cudaStream_t st);
+
 // Kernel launchers (les_kernels.cu, les_stage.cu), all asynchronous on `st`.
 template <typename real> struct Launch {
     static void metrics(const double *x, const double *y, const double *z, int ni, int nj, int nk,

@@ -190,58 +190,91 @@ __device__ __forceinline__ Prim64 prim_of(const double Q[5], double g)
     return s;
 }
 
+// Primitive state in the arithmetic type T of the boundary pass.
+template <typename T> struct PrimT {
+    T rho, u[3], p;
+};
+
+template <typename T> __device__ __forceinline__ void cons_t(const PrimT<T> &s, T g, T Q[5])
+{
+    Q[0] = s.rho;
+    Q[1] = s.rho * s.u[0];
+    Q[2] = s.rho * s.u[1];
+    Q[3] = s.rho * s.u[2];
+    Q[4] = s.p / (g - T(1)) + T(0.5) * s.rho * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+}
+
+template <typename T> __device__ __forceinline__ PrimT<T> prim_t(const T Q[5], T g)
+{
+    PrimT<T> s;
+    s.rho = Q[0];
+    for (int c = 0; c < 3; ++c) s.u[c] = Q[1 + c] / Q[0];
+    s.p = (g - T(1)) * (Q[4] - T(0.5) * Q[0] * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]));
+    return s;
+}
+
+// x^y in the precision P of the stored state: the isentropic density update
+// of the far-field condition is the only transcendental of the boundary pass,
+// and FP64 pow is slow on this GPU; the Riemann-invariant arithmetic, where
+// q_n,f ~ c_e - c_inf cancels, stays in FP64.
+template <typename P> __device__ __forceinline__ double bc_pow(double x, double y)
+{
+    return (double)pow((P)x, (P)y);
+}
+
 // Far field (Sec. "Far Field Boundary"): Riemann invariants along the unit
 // outward normal n; R- from the ambient at rest, R+ from the interior point.
-__device__ void bc_farfield(double g, double TR, const double Qe[5], const double n[3], double Qf[5])
+template <typename T, typename P = T>
+__device__ void bc_farfield(T g, T TR, const T Qe[5], const T n[3], T Qf[5])
 {
-    Prim64 e = prim_of(Qe, g);
-    const double pinf = 1.0 / g, rinf = TR;
-    const double ce = sqrt(g * e.p / e.rho), cinf = sqrt(g * pinf / rinf);
-    const double qne = e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2];
-    const double rp = qne + 2.0 * ce / (g - 1.0);
-    const double rm = 0.0 - 2.0 * cinf / (g - 1.0);
-    const double qnf = 0.5 * (rp + rm);
-    const double cf = 0.25 * (g - 1.0) * (rp - rm);
-    const double mn = qne / ce;
-    Prim64 f;
-    if (mn >= 1.0) {
+    const PrimT<T> e = prim_t(Qe, g);
+    const T pinf = T(1) / g, rinf = TR;
+    const T ce = sqrt(g * e.p / e.rho), cinf = sqrt(g * pinf / rinf);
+    const T qne = e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2];
+    const T rp = qne + T(2) * ce / (g - T(1));
+    const T rm = T(0) - T(2) * cinf / (g - T(1));
+    const T qnf = T(0.5) * (rp + rm);
+    const T cf = T(0.25) * (g - T(1)) * (rp - rm);
+    const T mn = qne / ce;
+    PrimT<T> f;
+    if (mn >= T(1)) {
         for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
         return;
     }
-    if (mn <= -1.0) {
+    if (mn <= T(-1)) {
         f.rho = rinf;
-        f.u[0] = f.u[1] = f.u[2] = 0.0;
+        f.u[0] = f.u[1] = f.u[2] = T(0);
         f.p = pinf;
-        cons_of(f, g, Qf);
+        cons_t(f, g, Qf);
         return;
     }
-    if (mn >= 0.0) { // subsonic outflow: entropy and tangential velocity from inside
+    if (mn >= T(0)) { // subsonic outflow: entropy and tangential velocity from inside
         for (int c = 0; c < 3; ++c) f.u[c] = e.u[c] + (qnf - qne) * n[c];
-        f.rho = pow(pow(e.rho, g) * cf * cf / (g * e.p), 1.0 / (g - 1.0));
+        f.rho = bc_pow<P>(bc_pow<P>(e.rho, g) * cf * cf / (g * e.p), T(1) / (g - T(1)));
     } else { // subsonic inflow: from the ambient (q_n,inf = 0)
-        for (int c = 0; c < 3; ++c) f.u[c] = 0.0 + (qnf - 0.0) * n[c];
-        f.rho = pow(pow(rinf, g) * cf * cf / (g * pinf), 1.0 / (g - 1.0));
+        for (int c = 0; c < 3; ++c) f.u[c] = T(0) + (qnf - T(0)) * n[c];
+        f.rho = bc_pow<P>(bc_pow<P>(rinf, g) * cf * cf / (g * pinf), T(1) / (g - T(1)));
     }
     f.p = f.rho * cf * cf / g;
-    cons_of(f, g, Qf);
+    cons_t(f, g, Qf);
 }
 
 // Exit (Sec. "Exit Boundary Condition").
-__device__ void bc_exit(double g, const double Qe[5], const double n[3], double Qf[5])
+template <typename T> __device__ void bc_exit(T g, const T Qe[5], const T n[3], T Qf[5])
 {
-    Prim64 e = prim_of(Qe, g);
-    const double ce = sqrt(g * e.p / e.rho);
-    if ((e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2]) / ce >= 1.0) {
+    const PrimT<T> e = prim_t(Qe, g);
+    const T ce = sqrt(g * e.p / e.rho);
+    if ((e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2]) / ce >= T(1)) {
         for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
         return;
     }
-    const double ei = e.p / ((g - 1.0) * e.rho);
-    const double rho = (1.0 / g) / ((g - 1.0) * ei);
+    const T ei = e.p / ((g - T(1)) * e.rho);
+    const T rho = (T(1) / g) / ((g - T(1)) * ei);
     Qf[0] = rho;
     Qf[1] = rho * e.u[0];
     Qf[2] = rho * e.u[1];
     Qf[3] = rho * e.u[2];
-    Qf[4] = rho * (ei + 0.5 * (e.u[0] * e.u[0] + e.u[1] * e.u[1] + e.u[2] * e.u[2]));
+    Qf[4] = rho * (ei + T(0.5) * (e.u[0] * e.u[0] + e.u[1] * e.u[1] + e.u[2] * e.u[2]));
 }
 
 // SplitMix64: output number n of the generator seeded with `seed`.
@@ -280,37 +313,38 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         const long long E = lidx(J, qe[0], qe[1], qe[2]);
         const long long fs = J.fs;
         real *Qd = J.q[dst];
-        const double g = J.gamma;
+        using T = double; // boundary arithmetic in FP64 (transcendental pow in the state precision)
+        const T g = (T)J.gamma;
         // unit outward normal from the face point's metric row
-        double n[3], nn = 0.0;
-        const double sg = side ? 1.0 : -1.0;
+        T n[3], nn = T(0);
+        const T sg = side ? T(1) : T(-1);
         for (int c = 0; c < 3; ++c) {
-            n[c] = sg * (double)J.met[(3 * axis + c) * fs + F];
+            n[c] = sg * J.met[(3 * axis + c) * fs + F];
             nn += n[c] * n[c];
         }
         nn = sqrt(nn);
         for (int c = 0; c < 3; ++c) n[c] /= nn;
-        const double jinvE = J.jinv64[E], jinvF = J.jinv64[F];
-        double Qe[5], Qf[5];
-        for (int f = 0; f < 5; ++f) Qe[f] = (double)Qd[f * fs + E] / jinvE;
+        const T jinvE = (T)J.jinv64[E], jinvF = (T)J.jinv64[F];
+        T Qe[5], Qf[5];
+        for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] / jinvE;
         if (type == LES_BC_FARFIELD) {
-            bc_farfield(g, J.TR, Qe, n, Qf);
+            bc_farfield<T, real>(g, (T)J.TR, Qe, n, Qf);
         } else if (type == LES_BC_EXIT) {
-            bc_exit(g, Qe, n, Qf);
+            bc_exit<T>(g, Qe, n, Qf);
         } else if (type == LES_BC_INFLOW_JET) {
             const int jj = qf[1], kk = qf[2];
-            const double rr = J.inflow_r[(long long)kk * J.n[1] + jj];
-            const double ut = 0.5 * (1.0 + tanh((0.5 - rr) / (2.0 * J.theta)));
-            if (ut < 0.01) {
-                bc_farfield(g, J.TR, Qe, n, Qf);
+            const T rr = (T)J.inflow_r[(long long)kk * J.n[1] + jj];
+            const T ut = T(0.5) * (T(1) + tanh((T(0.5) - rr) / (T(2) * (T)J.theta)));
+            if (ut < T(0.01)) {
+                bc_farfield<T, real>(g, (T)J.TR, Qe, n, Qf);
             } else {
-                const double M = J.mach;
-                const double T = (1.0 / J.TR) * (1.0 - ut) + ut + 0.5 * (g - 1.0) * M * M * ut * (1.0 - ut);
-                Prim64 s;
-                s.p = 1.0 / g;
-                s.rho = g * s.p / T;
+                const T M = (T)J.mach;
+                const T Tt = (T(1) / (T)J.TR) * (T(1) - ut) + ut + T(0.5) * (g - T(1)) * M * M * ut * (T(1) - ut);
+                PrimT<T> s;
+                s.p = T(1) / g;
+                s.rho = g * s.p / Tt;
                 s.u[0] = M * ut;
-                s.u[1] = s.u[2] = 0.0;
+                s.u[1] = s.u[2] = T(0);
                 if (level > 0) {
                     for (int c = 0; c < 3; ++c) {
                         unsigned long long ctr =
@@ -318,10 +352,10 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
                                (unsigned long long)kk) * (unsigned long long)J.n[1] +
                               (unsigned long long)jj) * 3ull) + (unsigned long long)c;
                         double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
-                        s.u[c] += J.noise_amp * M * (2.0 * h - 1.0);
+                        s.u[c] += (T)(J.noise_amp * J.mach * (2.0 * h - 1.0));
                     }
                 }
-                cons_of(s, g, Qf);
+                cons_t(s, g, Qf);
             }
         } else {
             continue;

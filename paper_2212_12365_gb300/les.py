@@ -32,7 +32,7 @@ EXPORTED = [
     "les_set_state_jet", "les_step", "les_get_state", "les_get_state_jet", "les_set_time",
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
-    "les_last_launch_count", "les_diag_sums_noalloc",
+    "les_last_launch_count", "les_diag_sums_noalloc", "les_describe",
     "les_last_error", "les_destroy",
 ]
 
@@ -96,6 +96,8 @@ def lib():
         L.les_last_launch_count.argtypes = [vp]
         L.les_last_launch_count.restype = ctypes.c_int64
         L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.les_describe.argtypes = [vp]
+        L.les_describe.restype = ctypes.c_char_p
         L.les_last_error.argtypes = [vp]
         L.les_last_error.restype = ctypes.c_char_p
         L.les_destroy.argtypes = [vp]
@@ -258,6 +260,10 @@ def les_profile_step(h, nsteps: int):
     cnt = (ctypes.c_int64 * len(KERNEL_KINDS))()
     _check(h, lib().les_profile_step(h, int(nsteps), _dptr(ms), cnt))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def les_describe(h) -> str:
+    return (lib().les_describe(h) or b"").decode()
 
 
 def les_last_launch_count(h) -> int:
