@@ -149,7 +149,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
         off = align_up(off + b, 256);
         return o;
     };
-    size_t o_met = take(NMET * fb);
+    size_t o_met = take((prec == LES_FP64 ? NMET64 : NMET) * fb);
     size_t o_j64 = prec == LES_FP32 ? take((size_t)J.fs * 8) : 0;
     size_t o_q0 = take(NF * fb);
     size_t o_q1 = take(NF * fb);
@@ -271,7 +271,7 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
     Launch<real>::metrics(dx, dy, dz, J.n[0], J.n[1], J.n[2], J.per, J.shift, met64, J.fs, J.pitch,
                           J.prm.Cs, h->st);
     CK(cudaGetLastError());
-    Launch<real>::static_fields(met64, J.fs, J.pitch, J.n, J.per, h->st);
+    Launch<real>::static_fields(met64, J.fs, J.pitch, J.n, J.per, h->prec == LES_FP64 ? 1 : 0, h->st);
     CK(cudaGetLastError());
     if (h->prec == LES_FP32) {
         Launch<real>::convert_metrics(met64, J.fs, (real *)J.met, J.fs, J.npad, h->st);
@@ -560,6 +560,8 @@ template <typename real>
 static int rhs_pass(les_handle *h, const BlockMap &pt, const JetDev<real> *jets, int src,
                     int rhs_only, int dst, int stage)
 {
+    // the four-kernel stage needs the FP64 interface tables
+    if (h->prec != LES_FP64) return fail(h, LES_ERR_STATE, "four-kernel stage on an FP32 handle");
     int gp = grid_cap(h, pt.total);
     Launch<real>::point(jets, pt, src, gp, h->st);
     Launch<real>::grads(jets, pt, gp, h->st);
@@ -880,10 +882,11 @@ static int autotune_fused(les_handle *h)
             for (int kc : kcs) {
                 int rc = set_fused_tiling(h, ty, kc);
                 if (rc) return rc;
-                fused_launch(h, -1, 0, 0, 0, 1, h->st); // warm-up
+                // real stage launches from Q(0) into the first stage register,
+                // which holds no state between steps
+                fused_launch(h, -1, 0, 1, 0, 0, h->st); // warm-up
                 CK(cudaEventRecord(e0, h->st));
-                fused_launch(h, -1, 0, 0, 0, 1, h->st);
-                fused_launch(h, -1, 0, 0, 0, 1, h->st);
+                for (int rep = 0; rep < 3; ++rep) fused_launch(h, -1, 0, 1, 0, 0, h->st);
                 CK(cudaEventRecord(e1, h->st));
                 CK(cudaEventSynchronize(e1));
                 float ms = 0;
@@ -897,7 +900,8 @@ static int autotune_fused(les_handle *h)
         cudaEventDestroy(e1);
         it = g_tune_cache.emplace(key, pick).first;
     }
-    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" + std::to_string(it->second.second);
+    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" + std::to_string(it->second.second) +
+                   " (tuned over ty {16,8} x kc {8,16,24,48,96,all})";
     return set_fused_tiling(h, it->second.first, it->second.second);
 }
 

@@ -18,13 +18,20 @@ constexpr int NF = 5;         // conserved variables
 // precision): the nine metric cofactors J^-1 d xi^a / d x_c at [3a + c],
 // J^-1, (Cs Delta)^2, J, and per axis a: the J^-1 average of the interface
 // to the +a neighbour, its reciprocal, and |row a| = sqrt(sum_c m_ac^2).
-constexpr int NMET = 21;
+constexpr int NMET = 21;      // fields of every precision
+constexpr int MET_A0 = 21;    // FP64 only: 27 interface tables, see below
+constexpr int NMET64 = 48;
 constexpr int MET_JINV = 9;
 constexpr int MET_CSD2 = 10;
 constexpr int MET_J = 11;
 constexpr int MET_JB = 12;    // + a
 constexpr int MET_RJB = 15;   // + a
 constexpr int MET_NORM = 18;  // + a
+// FP64 only, per axis a at [MET_A0 + 9a + 3b + c]: the interface (to the +a
+// neighbour) average of the cofactor J^-1 d xi^b / d x_c divided by the
+// interface J^-1, times 1/2 for b != a: the chain-rule weights of the compact
+// viscous flux applied to the normal difference (b == a) and to the SUM of
+// the two points' central differences (b != a).
 // Per-point stage fields: primitives, Sutherland viscosity, lambda-bar,
 // the unscaled conserved vector W0..W3 (= rho is P_RHO) and rho H = e + p,
 // and the inviscid point fluxes F_a (5 each) at P_F0 + 5a + f.
@@ -194,7 +201,7 @@ template <typename real> struct Launch {
     static void convert_metrics(const double *met64, long long fs64, real *met, long long fs,
                                 long long npad, cudaStream_t st);
     static void static_fields(double *met64, long long fs64, int pitch, const int n[3],
-                              const int per[3], cudaStream_t st);
+                              const int per[3], int iface_tables, cudaStream_t st);
     static void point(const JetDev<real> *jets, BlockMap bm, int src, int grid, cudaStream_t st);
     static void grads(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st);
     static void iface(const JetDev<real> *jets, BlockMap bm, int grid, cudaStream_t st);

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
 // axis a the interface average of J^-1 towards the +a neighbour, its
 // reciprocal, and the norm of metric row a.
 __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long fs, int pitch, int ni,
-                                                         int nj, int nk, int p0, int p1, int p2)
+                                                         int nj, int nk, int p0, int p1, int p2,
+                                                         int iface_tables)
 {
     const int n[3] = {ni, nj, nk};
     const int per[3] = {p0, p1, p2};
@@ -151,6 +152,14 @@ __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long 
             const double mx = met[(3 * a) * fs + o], my = met[(3 * a + 1) * fs + o],
                          mz = met[(3 * a + 2) * fs + o];
             met[(MET_NORM + a) * fs + o] = sqrt(mx * mx + my * my + mz * mz);
+            if (iface_tables) {
+                const double rjb = 1.0 / jb;
+                for (int b = 0; b < 3; ++b)
+                    for (int c = 0; c < 3; ++c) {
+                        const double mc = 0.5 * (met[(3 * b + c) * fs + o] + met[(3 * b + c) * fs + oR]);
+                        met[(MET_A0 + 9 * a + 3 * b + c) * fs + o] = mc * rjb * (b == a ? 1.0 : 0.5);
+                    }
+            }
         }
     }
 }
@@ -673,10 +682,10 @@ void Launch<real>::metrics(const double *x, const double *y, const double *z, in
 
 template <typename real>
 void Launch<real>::static_fields(double *met64, long long fs64, int pitch, const int n[3],
-                                 const int per[3], cudaStream_t st)
+                                 const int per[3], int iface_tables, cudaStream_t st)
 {
     k_static_fields<<<grid_for((long long)n[0] * n[1] * n[2]), BLOCK, 0, st>>>(
-        met64, fs64, pitch, n[0], n[1], n[2], per[0], per[1], per[2]);
+        met64, fs64, pitch, n[0], n[1], n[2], per[0], per[1], per[2], iface_tables);
 }
 
 template <typename real>

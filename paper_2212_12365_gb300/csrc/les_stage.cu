@@ -28,6 +28,24 @@ namespace les {
 
 __constant__ double c_alpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
 
+// Reciprocal.  FP32 uses the hardware division.  In FP64, whose pipe is the
+// bottleneck on this GPU, the reciprocal is a Newton-Raphson iteration
+// r <- r (2 - b r) from a single-precision seed: each step squares the
+// relative error of the 24-bit seed, so two steps reach double rounding (a
+// unit in the last place), at fewer FP64 operations than an IEEE division.
+// Arguments are positive normal numbers (densities, temperatures, sensor
+// denominators).  Square roots stay the native ones (an iteration from a
+// single-precision seed measured slower, and must special-case zero strain).
+template <typename real> __device__ __forceinline__ real rcp_(real b) { return real(1) / b; }
+template <> __device__ __forceinline__ double rcp_<double>(double b)
+{
+    double r = (double)__frcp_rn((float)b);
+    double e = fma(-b, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-b, r, 1.0);
+    return fma(r, e, r);
+}
+
 // ---------------------------------------------------------------------------
 // k_point
 // ---------------------------------------------------------------------------
@@ -51,13 +69,13 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
         const real rho = Q[lp] * rj;
         const real ru = Q[fs + lp] * rj, rv = Q[2 * fs + lp] * rj, rw = Q[3 * fs + lp] * rj;
         const real e = Q[4 * fs + lp] * rj;
-        const real rrho = real(1) / rho;
+        const real rrho = rcp_<real>(rho);
         const real u = ru * rrho, v = rv * rrho, w = rw * rrho;
         const real p = (gam - real(1)) * (e - real(0.5) * (ru * u + rv * v + rw * w));
         const real T = gam * p * rrho;
         const real sT = sqrt(T); // speed of sound: c^2 = gamma p / rho = T in jet units
         const real S = (real)J.suth_S;
-        const real mu = T * sT * (real(1) + S) / (T + S);
+        const real mu = T * sT * (real(1) + S) * rcp_<real>(T + S);
         const real rH = e + p;
         real lam[3];
 #pragma unroll
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict_
             const real pm = P[P_P * fs + lidx(J, rm[0], rm[1], rm[2])];
             const real p0 = P[P_P * fs + lidx(J, r0[0], r0[1], r0[2])];
             const real pp = P[P_P * fs + lidx(J, rp[0], rp[1], rp[2])];
-            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) / (pp + real(2) * p0 + pm);
+            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) * rcp_<real>(pp + real(2) * p0 + pm);
         }
 #pragma unroll
         for (int f = 0; f < 4; ++f)
@@ -225,28 +243,32 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
         H[f] = real(0.5) * (F[L] + F[R]) - (se2 * dW0 - se4 * d3);
     }
     // compact viscous + SGS flux: normal derivative from the two points,
-    // tangential derivatives averaged, coefficients/metrics/velocity averaged
-    real dphi[4][3];
+    // tangential derivatives averaged, coefficients/metrics/velocity averaged.
+    // A = interface tables (cofactor average / interface J^-1, 1/2 folded into
+    // the tangential rows), so grad phi = sum_b A_b D_b with D_a = phi_R - phi_L
+    // and D_b = the sum of the two points' central differences (b != a); the
+    // averaged cofactor row a is A_a times the interface J^-1, folded into the
+    // transport coefficients.
+    const real *__restrict__ A = M + (MET_A0 + 9 * a) * fs + L;
+    real D[4][3];
     const int pf[4] = {P_U, P_V, P_W, P_T};
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            dphi[f][b] = (b == a) ? P[pf[f] * fs + R] - P[pf[f] * fs + L]
-                                  : real(0.5) * (G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R]);
-    real mc[9];
-    const real rjb = M[(MET_RJB + a) * fs + L];
+            D[f][b] = (b == a) ? P[pf[f] * fs + R] - P[pf[f] * fs + L]
+                               : G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R];
+    real Ab[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) mc[t] = real(0.5) * (M[t * fs + L] + M[t * fs + R]);
+    for (int t = 0; t < 9; ++t) Ab[t] = A[t * fs];
     real gu[4][3];
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            gu[f][c] = (mc[c] * dphi[f][0] + mc[3 + c] * dphi[f][1] + mc[6 + c] * dphi[f][2]) * rjb;
+        for (int c = 0; c < 3; ++c) gu[f][c] = Ab[c] * D[f][0] + Ab[3 + c] * D[f][1] + Ab[6 + c] * D[f][2];
     const real div3 = (gu[0][0] + gu[1][1] + gu[2][2]) * real(1.0 / 3.0);
-    const real coef = G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]; // 2 x average
-    const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]);
+    const real coef = (G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]) * jb; // 2 x average x J^-1
+    const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]) * jb;
     real tau[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -260,7 +282,7 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     const real vb[3] = {real(0.5) * (P[P_U * fs + L] + P[P_U * fs + R]),
                         real(0.5) * (P[P_V * fs + L] + P[P_V * fs + R]),
                         real(0.5) * (P[P_W * fs + L] + P[P_W * fs + R])};
-    const real *mr = mc + 3 * a;
+    const real *mr = Ab + 3 * a;
 #pragma unroll
     for (int i = 0; i < 3; ++i) H[1 + i] -= mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
     real fe = real(0);
