@@ -38,13 +38,19 @@ FLOPS_PER_PT_STAGE = {"point": 96, "grads": 141, "iface": 765, "update": 41}
 ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4}
 # DRAM bytes per point of one launch of the dominant kernel, from the ncu
 # captures summarised in profiles/ (None once the kernel changed since).
-TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 789.0}
+TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 871.0, ("fp32", "k_fused"): 98.4}
 # Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+def _batch64():
+    jets = I.batch_jets(64, seed=4)
+    return [g for g, _ in jets], [f for _, f in jets]
+
+
 WORKLOADS = {
     "jet-384x256x144": (I.jet_paper_scale, "fp64"),
+    "batch-64": (_batch64, "fp32"),
     "jet-768x384x192": (I.jet_large, "fp32"),
     "jet-48x32x32": (I.jet_small, "fp64"),
     "jet-192x128x72": (I.jet_medium, "fp64"),
@@ -109,6 +115,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_rate(local_ms, points_per_rank, steps, ws, device):
+    """Whole-job rate of ws replicas: all ranks' point-stage updates divided by
+    the slowest rank's time (max over ranks by all-reduce)."""
+    ms = float(local_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ws * points_per_rank * 5 * steps / (ms / 1e3), ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -155,6 +174,8 @@ def run_reference(args):
         return
     make, prec = WORKLOADS[args.workload]
     spec, fp = make()
+    if isinstance(spec, list):  # a batch: the oracle samples its first jet
+        spec, fp = spec[0], fp[0]
     import oracle  # noqa: F401
     oracle.build()
     vals = []
@@ -177,6 +198,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def precision_form(args, spec, fp, les, torch, fp64_value):
+    """FP32 storage/arithmetic on the same grid (metrics and sums in FP64): its
+    rate, speedup over the FP64 path, and relative L2 per field against the FP64
+    path after the same number of steps from the ambient start."""
+    out = {}
+    states = {}
+    steps = args.warmup + args.steps
+    for prec in (les.LES_FP32, les.LES_FP64):
+        s = les.Solver(spec, fp, prec)
+        s.set_state(I.ambient_primitives(spec.N, fp.TR), les.LES_STATE_PRIMITIVE)
+        if prec == les.LES_FP32:
+            s.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st = torch.cuda.current_stream()
+            e0.record(st)
+            s.step(args.steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out = {"precision": "fp32", "value": spec.N * 5 * args.steps / (ms / 1e3),
+                   "ms_per_step": ms / args.steps, "stage": les.les_describe(s.h)}
+        else:
+            s.step(steps)
+        states[prec] = s.get_state(les.LES_STATE_CONSERVED)
+        s.close()
+    a, b = states[les.LES_FP32], states[les.LES_FP64]
+    err = np.sqrt(((a - b) ** 2).sum(axis=1) / np.maximum((b ** 2).sum(axis=1), 1e-300))
+    out["speedup_vs_fp64"] = out["value"] / fp64_value
+    out["rel_l2_vs_fp64_per_field"] = [float(e) for e in err]
+    out["after_steps"] = steps
+    out["hbm_frac_algorithmic"] = out["value"] * ALGO_BYTES_PER_PT_STAGE["fp32"] / 1e9 / \
+        measured_peaks().get("hbm_gbs", 6750.0)
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -192,12 +249,25 @@ def run_ours(args):
     prec = args.precision or prec_default
     P = les.LES_FP64 if prec == "fp64" else les.LES_FP32
     spec, fp = make()
-    fp.seed = fp.seed + 1000 * rank
-    N = spec.N
-    prim = I.ambient_primitives(N, fp.TR)
+    batch = isinstance(spec, list)
+    specs = spec if batch else [spec]
+    fps = fp if batch else [fp]
+    for f in fps:
+        f.seed = f.seed + 1000 * rank
+    N = sum(g.N for g in specs)
     stream = torch.cuda.current_stream()
-    solver = les.Solver(spec, fp, P, stream=les.ctypes.c_void_p(stream.cuda_stream))
-    solver.set_state(prim, les.LES_STATE_PRIMITIVE)
+    solver = les.Solver(specs if batch else spec, fps if batch else fp, P,
+                        stream=les.ctypes.c_void_p(stream.cuda_stream))
+    for j, (g, f) in enumerate(zip(specs, fps)):
+        solver.set_state(I.ambient_primitives(g.N, f.TR), les.LES_STATE_PRIMITIVE, jet=j)
+    probe = None
+    if args.probe or args.workload == "jet-768x384x192":
+        # cylinder r = 3D, 256 azimuths x 384 axial stations, every 5 steps
+        xyz = I.cylinder_points(3.0, 256, 384, 0.5, specs[0].x.max() - 0.5)
+        cap = 64
+        probe = torch.zeros((cap, 5, xyz.shape[1]), device="cuda",
+                            dtype=torch.float64 if P == les.LES_FP64 else torch.float32)
+        les.les_probe_surface(solver.h, xyz, 5, probe.data_ptr(), cap)
     # a developed state: march the start-up before timing
     solver.step(args.warmup)
     torch.cuda.synchronize()
@@ -215,14 +285,8 @@ def run_ours(args):
         solver.step(args.steps)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
     launches = les.les_last_launch_count(solver.h)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N * 5 * args.steps / (ms / 1e3)
+    value, ms = aggregate_rate(ev0.elapsed_time(ev1), N, args.steps, ws, "cuda")
 
     # per-kernel device time of the same stage sequence, eager with events
     prof = les.les_profile_step(solver.h, max(1, min(args.steps, 3)))
@@ -254,7 +318,7 @@ def run_ours(args):
 
     # end to end through the public API: pinned host state in, step, state out
     e2e = None
-    if not args.no_e2e and ws == 1:
+    if not args.no_e2e and ws == 1 and not batch:
         host_in = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
         host_out = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
         host_in.numpy()[:] = solver.get_state(les.LES_STATE_RAW)
@@ -273,10 +337,12 @@ def run_ours(args):
                "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8, "steps": ke}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not batch:
         cpu = cpu_baseline(spec, fp)
+    secondary = None
+    if rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64" and not args.no_fp32:
+        secondary = precision_form(args, spec, fp, les, torch, value)
 
-    solver.close()
     if rank == 0:
         line = {"metric": "grid-point-stage updates/s", "value": value,
                 "unit": "grid-point-stage updates/s", "n_gpus": ws, "steps": args.steps,
@@ -284,12 +350,20 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "precision": prec, "points": N,
-                           "grid": list(spec.dims), "mach_j": fp.mach_j, "TR": fp.TR, "Re_D": fp.Re,
+                           "grid": [list(g.dims) for g in specs] if batch else list(spec.dims),
+                           "jets": len(specs),
+                           "mach_j": [f.mach_j for f in fps] if batch else fp.mach_j,
+                           "TR": [round(f.TR, 3) for f in fps] if batch else fp.TR,
+                           "Re_D": [round(f.Re) for f in fps] if batch else fp.Re,
+                           "probe": None if probe is None else {"points": int(probe.shape[2]), "every": 5,
+                                                                 "frames": les.les_probe_frames(solver.h)},
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "inputs larger than L2 (state + metrics + scratch are GBs)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "precision_form": secondary,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+    solver.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -305,6 +379,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 line of the FP64 default run")
+    ap.add_argument("--probe", action="store_true", help="register the cylinder surface probe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
