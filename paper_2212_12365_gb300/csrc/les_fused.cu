@@ -12,14 +12,18 @@
 // to its +i neighbour (the -i one comes from the lane below by a warp
 // shuffle), the eta-interface to its +j neighbour (the -j one from shared
 // memory) and the zeta-interface to its +k neighbour (the -k one is carried
-// in registers while marching along k).  Point data live in a ring of 5
-// planes over R2 = R1 plus one column/row on each side, so that derivatives
-// — one-sided at a non-periodic end included — of plane k are formed when
-// plane k+2 arrives; derivatives, transport coefficients, sensors and
-// lambda-bar of R1 are kept for two planes.  The 32 x 8 variant fits two CTAs
-// per SM, so the load phase of one overlaps the arithmetic of the other.
-// Per loaded plane kL:  load+primitives(kL) | gradients(kL-2) |
-// interfaces+update(kL-3).
+// in registers while marching along k).  All three have this thread's point
+// on their low side, so its data are read from shared memory once per plane.
+// Point data live in a ring of 5 planes over R2 = R1 plus one column/row on
+// each side, so that derivatives — one-sided at a non-periodic end included —
+// of plane k are formed when plane k+2 arrives; derivatives, transport
+// coefficients, sensors, lambda-bar and metrics of R1 are kept for two
+// planes.  Shared memory holds cells as float4/float2 records so that one
+// vector load fetches a point's primitives, derivatives or metric row
+// (the stage is issue-bound, and this cuts load instructions about 3x).
+// Per loaded plane kL:  load+primitives(kL), metrics(kL-2) | gradients(kL-2)
+// | interfaces+update(kL-3).  The 32 x 8 variant fits two CTAs per SM, so the
+// load phase of one overlaps the arithmetic of the other.
 //
 // Work list.  Items (jet, tile x, tile y, k-chunk) are walked by a persistent
 // grid in a fixed order; results do not depend on the item order, the chunk
@@ -32,24 +36,42 @@ namespace les {
 
 namespace {
 
-constexpr int FX = 32;  // threads along i (one warp per row)
-constexpr int NPF = 6;  // point fields in the ring: rho u v w p T
-constexpr int NGF = 20; // R1 fields: 12 derivatives, mu_eff, kappa, nu x3, lambda-bar x3
-enum { GF_MUEFF = 12, GF_KAP = 13, GF_NU = 14, GF_LAM = 17 };
-constexpr int NMF = 10; // R1 metric fields: 9 cofactors, J^-1
+constexpr int FX = 32; // threads along i (one warp per row)
 
 __constant__ float c_alpha_f[5] = {0.25f, 1.0f / 6.0f, 0.375f, 0.5f, 1.0f};
 
+// Shared-memory map (byte offsets).  float4 records first (16-byte aligned).
+//   PA [5][NC2] float4  rho u v w       (point ring)
+//   GD [2][3][NC1] float4  d(u,v,w,T)/d xi_a, a = 0..2
+//   GC [2][2][NC1] float4  (mu_eff, kappa, nu_xi, lb_xi), (nu_eta, lb_eta, nu_zeta, lb_zeta)
+//   MA [2][2][NC1] float4  metric cofactors m0..m3, m4..m7
+//   PB [5][NC2] float2  p T              (point ring)
+//   MB [2][NC1] float2  m8, J^-1
+//   SH [5][TY][FX] float  eta-interface fluxes of the current plane
 template <int TY> struct Geo {
     static constexpr int NT = FX * TY;
     static constexpr int C2X = FX + 2, C2Y = TY + 2, NC2 = C2X * C2Y; // R2: cells [-1, FX] x [-1, TY]
     static constexpr int NC1 = FX * TY;                                // R1: the thread grid
-    static constexpr int OFF_PRIM = 0;                          // [5][NPF][NC2]
-    static constexpr int OFF_GRAD = OFF_PRIM + 5 * NPF * NC2;   // [2][NGF][NC1]
-    static constexpr int OFF_MET = OFF_GRAD + 2 * NGF * NC1;    // [2][NMF][NC1]
-    static constexpr int OFF_HY = OFF_MET + 2 * NMF * NC1;      // [5][TY][FX]
-    static constexpr int FLOATS = OFF_HY + 5 * TY * FX;
-    static constexpr size_t BYTES = sizeof(float) * FLOATS;
+    static constexpr size_t O_PA = 0;
+    static constexpr size_t O_GD = O_PA + 16ull * 5 * NC2;
+    static constexpr size_t O_GC = O_GD + 16ull * 2 * 3 * NC1;
+    static constexpr size_t O_MA = O_GC + 16ull * 2 * 2 * NC1;
+    static constexpr size_t O_PB = O_MA + 16ull * 2 * 2 * NC1;
+    static constexpr size_t O_MB = O_PB + 8ull * 5 * NC2;
+    static constexpr size_t O_SH = O_MB + 8ull * 2 * NC1;
+    static constexpr size_t BYTES = O_SH + 4ull * 5 * TY * FX;
+};
+
+template <int TY> struct Sm {
+    float4 *PA, *GD, *GC, *MA;
+    float2 *PB, *MB;
+    float *SH;
+    __device__ __forceinline__ explicit Sm(unsigned char *b)
+        : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
+          GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
+          PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH))
+    {
+    }
 };
 
 __device__ __forceinline__ int ring5(int k) { return ((k % 5) + 5) % 5; }
@@ -62,81 +84,130 @@ __device__ __forceinline__ int gidx(int g, int n, int per)
     return (g >= 0 && g < n) ? g : -1;
 }
 
-// Flux through the interface between L and R along axis A.  Smem index
-// arguments: p* index the point ring (cell + slot offset), g* the R1 tables.
-template <int A, int TY>
-__device__ __forceinline__ void fused_iface(const float *__restrict__ S, const FusedParams &FP,
-                                            int pLm, int pL, int pR, int pRp, int gL, int gR, int mLi,
-                                            int mRi, bool lo_end, bool hi_end, float H[5])
+// Square root of a strictly positive argument through the hardware
+// reciprocal square root (max. 2 ulp): x * rsqrt(x).
+__device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+
+__device__ __forceinline__ float cmp(const float4 &v, int i)
 {
-    using G_ = Geo<TY>;
-    const float *SP = S + G_::OFF_PRIM;
-    const float *SG = S + G_::OFF_GRAD;
-    const float *SM = S + G_::OFF_MET;
-    constexpr int N2 = G_::NC2, N1 = G_::NC1;
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Dissipation vector W = [rho, rho u, rho v, rho w, e + p] of a point.
+__device__ __forceinline__ void wvec(const float4 &a, float p, float hg, float W[5])
+{
+    W[0] = a.x;
+    W[1] = a.x * a.y;
+    W[2] = a.x * a.z;
+    W[3] = a.x * a.w;
+    W[4] = hg * p + 0.5f * a.x * (a.y * a.y + a.z * a.z + a.w * a.w);
+}
+
+// Data of the thread's own point at the interface plane; it is the low
+// side (L) of all three interfaces the thread evaluates.
+struct OwnPt {
+    float4 a; // rho u v w
+    float p, T;
+    float m[9], jinv;
+    int c1, pl; // R1 cell and R1 plane (ring2) of the point
+};
+
+// Flux through the interface between the own point L and its +A neighbour R
+// (Eqs. spatial_discret, inv_flux_vec, dissip_term; compact viscous flux of
+// the interface).  Shared-memory indices: r2/lm2/rp2 of R, L-1 and R+1 in
+// the point ring; r1 of R in the R1 tables, rpl the R1 plane (ring2) of R.
+template <int A, int TY>
+__device__ __forceinline__ void fused_iface(const Sm<TY> &S, const FusedParams &FP, const OwnPt &L, int r2,
+                                            int lm2, int rp2, int r1, int rpl, bool lo_end, bool hi_end,
+                                            float H[5])
+{
+    constexpr int N1 = Geo<TY>::NC1;
     const float hg = FP.hgam;
-    // dissipation vector W = [rho, rho u, rho v, rho w, e + p] at the four points
-    float W[4][5];
-    const int pts[4] = {lo_end ? pL : pLm, pL, pR, hi_end ? pR : pRp};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int o = pts[t];
-        const float r = SP[o], u = SP[N2 + o], v = SP[2 * N2 + o], w = SP[3 * N2 + o], p = SP[4 * N2 + o];
-        W[t][0] = r;
-        W[t][1] = r * u;
-        W[t][2] = r * v;
-        W[t][3] = r * w;
-        W[t][4] = hg * p + 0.5f * r * (u * u + v * v + w * w);
+    float LW[5];
+    wvec(L.a, L.p, hg, LW);
+    // R point and the two outer points of the dissipation stencil
+    const float4 ra = S.PA[r2];
+    const float2 rb = S.PB[r2];
+    float WR[5], WLm[5], WRp[5];
+    wvec(ra, rb.x, hg, WR);
+    if (!lo_end) {
+        const float4 q = S.PA[lm2];
+        wvec(q, S.PB[lm2].x, hg, WLm);
     }
-    const float pLv = SP[4 * N2 + pL], pRv = SP[4 * N2 + pR];
-    // metric rows at L and R
-    float mL[9], mR[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        mL[t] = SM[t * N1 + mLi];
-        mR[t] = SM[t * N1 + mRi];
+    if (!hi_end) {
+        const float4 q = S.PA[rp2];
+        wvec(q, S.PB[rp2].x, hg, WRp);
     }
-    const float jL = SM[9 * N1 + mLi], jR = SM[9 * N1 + mRi];
-    const float jb = 0.5f * (jL + jR);
-    const float rjb = 1.0f / jb;
+    // metric rows at R
+    float mR[9];
+    const float4 u0 = S.MA[(rpl * 2 + 0) * N1 + r1], u1 = S.MA[(rpl * 2 + 1) * N1 + r1];
+    const float2 u2 = S.MB[rpl * N1 + r1];
+    mR[0] = u0.x; mR[1] = u0.y; mR[2] = u0.z; mR[3] = u0.w;
+    mR[4] = u1.x; mR[5] = u1.y; mR[6] = u1.z; mR[7] = u1.w;
+    mR[8] = u2.x;
+    const float jb = 0.5f * (L.jinv + u2.y);
     // centred inviscid flux 0.5 (F_L + F_R), J^-1 U = m_A . u
     {
-        const float JUL = mL[3 * A] * SP[N2 + pL] + mL[3 * A + 1] * SP[2 * N2 + pL] + mL[3 * A + 2] * SP[3 * N2 + pL];
-        const float JUR = mR[3 * A] * SP[N2 + pR] + mR[3 * A + 1] * SP[2 * N2 + pR] + mR[3 * A + 2] * SP[3 * N2 + pR];
-        H[0] = 0.5f * (W[1][0] * JUL + W[2][0] * JUR);
-        H[1] = 0.5f * (W[1][1] * JUL + pLv * mL[3 * A] + W[2][1] * JUR + pRv * mR[3 * A]);
-        H[2] = 0.5f * (W[1][2] * JUL + pLv * mL[3 * A + 1] + W[2][2] * JUR + pRv * mR[3 * A + 1]);
-        H[3] = 0.5f * (W[1][3] * JUL + pLv * mL[3 * A + 2] + W[2][3] * JUR + pRv * mR[3 * A + 2]);
-        H[4] = 0.5f * (W[1][4] * JUL + W[2][4] * JUR);
+        const float JUL = L.m[3 * A] * L.a.y + L.m[3 * A + 1] * L.a.z + L.m[3 * A + 2] * L.a.w;
+        const float JUR = mR[3 * A] * ra.y + mR[3 * A + 1] * ra.z + mR[3 * A + 2] * ra.w;
+        H[0] = 0.5f * (LW[0] * JUL + WR[0] * JUR);
+        H[1] = 0.5f * (LW[1] * JUL + L.p * L.m[3 * A] + WR[1] * JUR + rb.x * mR[3 * A]);
+        H[2] = 0.5f * (LW[2] * JUL + L.p * L.m[3 * A + 1] + WR[2] * JUR + rb.x * mR[3 * A + 1]);
+        H[3] = 0.5f * (LW[3] * JUL + L.p * L.m[3 * A + 2] + WR[3] * JUR + rb.x * mR[3 * A + 2]);
+        H[4] = 0.5f * (LW[4] * JUL + WR[4] * JUR);
+    }
+    // transport coefficients, sensor and lambda-bar at R
+    float mueR, kapR, nuR, lbR;
+    if (A == 0) {
+        const float4 c = S.GC[(rpl * 2 + 0) * N1 + r1];
+        mueR = c.x; kapR = c.y; nuR = c.z; lbR = c.w;
+    } else {
+        const float2 c = *reinterpret_cast<const float2 *>(&S.GC[(rpl * 2 + 0) * N1 + r1]);
+        const float2 e = reinterpret_cast<const float2 *>(&S.GC[(rpl * 2 + 1) * N1 + r1])[A - 1];
+        mueR = c.x; kapR = c.y; nuR = e.x; lbR = e.y;
+    }
+    float mueL, kapL, nuL, lbL;
+    if (A == 0) {
+        const float4 c = S.GC[(L.pl * 2 + 0) * N1 + L.c1];
+        mueL = c.x; kapL = c.y; nuL = c.z; lbL = c.w;
+    } else {
+        const float2 c = *reinterpret_cast<const float2 *>(&S.GC[(L.pl * 2 + 0) * N1 + L.c1]);
+        const float2 e = reinterpret_cast<const float2 *>(&S.GC[(L.pl * 2 + 1) * N1 + L.c1])[A - 1];
+        mueL = c.x; kapL = c.y; nuL = e.x; lbL = e.y;
     }
     // Turkel-Vatsa dissipation
     {
-        const float eps2 = FP.k2 * fmaxf(SG[(GF_NU + A) * N1 + gL], SG[(GF_NU + A) * N1 + gR]);
+        const float eps2 = FP.k2 * fmaxf(nuL, nuR);
         const float eps4 = fmaxf(0.0f, FP.k4 - eps2);
-        const float sc = jb * 0.5f * (SG[(GF_LAM + A) * N1 + gL] + SG[(GF_LAM + A) * N1 + gR]);
+        const float sc = jb * 0.5f * (lbL + lbR);
         const float se2 = sc * eps2, se4 = sc * eps4;
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
-            const float dW0 = W[2][f] - W[1][f];
-            const float dWp = hi_end ? -dW0 : W[3][f] - W[2][f];
-            const float dWm = lo_end ? -dW0 : W[1][f] - W[0][f];
+            const float dW0 = WR[f] - LW[f];
+            const float dWp = hi_end ? -dW0 : WRp[f] - WR[f];
+            const float dWm = lo_end ? -dW0 : LW[f] - WLm[f];
             const float d3 = dWp - 2.0f * dW0 + dWm;
             H[f] -= se2 * dW0 - se4 * d3;
         }
     }
     // compact viscous + SGS flux
     {
-        const int pf[4] = {1, 2, 3, 5}; // u v w T in the point ring
+        const float rjb = 1.0f / jb;
+        constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2; // tangential axes
+        const float4 dR1 = S.GD[(rpl * 3 + B1) * N1 + r1], dR2 = S.GD[(rpl * 3 + B2) * N1 + r1];
+        const float4 dL1 = S.GD[(L.pl * 3 + B1) * N1 + L.c1], dL2 = S.GD[(L.pl * 3 + B2) * N1 + L.c1];
         float dphi[4][3];
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                dphi[f][b] = (b == A) ? SP[pf[f] * N2 + pR] - SP[pf[f] * N2 + pL]
-                                      : 0.5f * (SG[(3 * f + b) * N1 + gL] + SG[(3 * f + b) * N1 + gR]);
+        for (int f = 0; f < 4; ++f) {
+            const float lv = f == 0 ? L.a.y : (f == 1 ? L.a.z : (f == 2 ? L.a.w : L.T));
+            const float rv = f == 0 ? ra.y : (f == 1 ? ra.z : (f == 2 ? ra.w : rb.y));
+            dphi[f][A] = rv - lv;
+            dphi[f][B1] = 0.5f * (cmp(dL1, f) + cmp(dR1, f));
+            dphi[f][B2] = 0.5f * (cmp(dL2, f) + cmp(dR2, f));
+        }
         float mc[9];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) mc[t] = 0.5f * (mL[t] + mR[t]);
+        for (int t = 0; t < 9; ++t) mc[t] = 0.5f * (L.m[t] + mR[t]);
         float gu[4][3];
 #pragma unroll
         for (int f = 0; f < 4; ++f)
@@ -144,8 +215,8 @@ __device__ __forceinline__ void fused_iface(const float *__restrict__ S, const F
             for (int c = 0; c < 3; ++c)
                 gu[f][c] = (mc[c] * dphi[f][0] + mc[3 + c] * dphi[f][1] + mc[6 + c] * dphi[f][2]) * rjb;
         const float div3 = (gu[0][0] + gu[1][1] + gu[2][2]) * (1.0f / 3.0f);
-        const float coef = SG[GF_MUEFF * N1 + gL] + SG[GF_MUEFF * N1 + gR];
-        const float kap = 0.5f * (SG[GF_KAP * N1 + gL] + SG[GF_KAP * N1 + gR]);
+        const float coef = mueL + mueR;
+        const float kap = 0.5f * (kapL + kapR);
         float tau[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -156,8 +227,7 @@ __device__ __forceinline__ void fused_iface(const float *__restrict__ S, const F
                 tau[c][i] = tau[i][c];
             }
         }
-        const float vb[3] = {0.5f * (SP[N2 + pL] + SP[N2 + pR]), 0.5f * (SP[2 * N2 + pL] + SP[2 * N2 + pR]),
-                             0.5f * (SP[3 * N2 + pL] + SP[3 * N2 + pR])};
+        const float vb[3] = {0.5f * (L.a.y + ra.y), 0.5f * (L.a.z + ra.z), 0.5f * (L.a.w + ra.w)};
         const float *mr = mc + 3 * A;
 #pragma unroll
         for (int i = 0; i < 3; ++i) H[1 + i] -= mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
@@ -169,6 +239,38 @@ __device__ __forceinline__ void fused_iface(const float *__restrict__ S, const F
     }
 }
 
+// Derivative along one axis of (u, v, w, T) and the pressure sensor of the
+// point at ring offset 0, from the points at offsets -s, 0, +s (central) or,
+// at a non-periodic end, the one-sided second-order stencil (the sensor of
+// an end point is its interior neighbour's: same three points).
+struct D3 {
+    float4 d;
+    float nu;
+};
+
+__device__ __forceinline__ D3 deriv_central(const float4 &am, const float2 &bm, float p0, const float4 &ap,
+                                            const float2 &bp)
+{
+    D3 r;
+    r.d = make_float4(0.5f * (ap.y - am.y), 0.5f * (ap.z - am.z), 0.5f * (ap.w - am.w), 0.5f * (bp.y - bm.y));
+    r.nu = __fdividef(fabsf(bp.x - 2.0f * p0 + bm.x), bp.x + 2.0f * p0 + bm.x);
+    return r;
+}
+
+// Points q1, q2, q3 at offsets (t-1, t, t+1) s, t = +1 (start) or -1 (end).
+__device__ __forceinline__ D3 deriv_end(int t, const float4 &a1, const float2 &b1, const float4 &a2,
+                                        const float2 &b2, const float4 &a3, const float2 &b3)
+{
+    // forward  (t = +1): -1.5 q(0) + 2 q(s) - 0.5 q(2s)  = -1.5 q1 + 2 q2 - 0.5 q3
+    // backward (t = -1):  1.5 q(0) - 2 q(-s) + 0.5 q(-2s) = 0.5 q1 - 2 q2 + 1.5 q3
+    const float c1 = t > 0 ? -1.5f : 0.5f, c2 = t > 0 ? 2.0f : -2.0f, c3 = t > 0 ? -0.5f : 1.5f;
+    D3 r;
+    r.d = make_float4(c1 * a1.y + c2 * a2.y + c3 * a3.y, c1 * a1.z + c2 * a2.z + c3 * a3.z,
+                      c1 * a1.w + c2 * a2.w + c3 * a3.w, c1 * b1.y + c2 * b2.y + c3 * b3.y);
+    r.nu = __fdividef(fabsf(b3.x - 2.0f * b2.x + b1.x), b3.x + 2.0f * b2.x + b1.x);
+    return r;
+}
+
 } // namespace
 
 template <int TY>
@@ -177,13 +279,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only)
 {
     using G_ = Geo<TY>;
-    extern __shared__ float S[];
-    float *SP = S + G_::OFF_PRIM;
-    float *SG = S + G_::OFF_GRAD;
-    float *SM = S + G_::OFF_MET;
-    float *SH = S + G_::OFF_HY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Sm<TY> S(smem_raw);
     constexpr int N2 = G_::NC2, N1 = G_::NC1, C2X = G_::C2X;
-    constexpr int PSLOT = NPF * N2; // floats per ring slot
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
     // this thread's R1 cell is (tx, ty); its R2 cell:
@@ -230,6 +328,8 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                              (jb + ty) < jhi;
         const bool xi_ok = col_ok && tx <= FX - 2 && ty >= 1 && ty <= TY - 2 && (pi || gi < ni - 1);
         const bool eta_ok = col_ok && tx >= 1 && tx <= FX - 2 && ty <= TY - 2 && (pj || gj < nj - 1);
+        const bool xi_lo = !pi && gi == 0, xi_hi = !pi && gi + 1 == ni - 1;
+        const bool eta_lo = !pj && gj == 0, eta_hi = !pj && gj + 1 == nj - 1;
         // in-plane derivative stencils of this cell (central unless at a non-periodic end)
         const int ti = (!pi && gi == 0) ? 1 : ((!pi && gi == ni - 1) ? -1 : 0);
         const int tj = (!pj && gj == 0) ? 1 : ((!pj && gj == nj - 1) ? -1 : 0);
@@ -262,11 +362,32 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
             for (int t = 0; t < 5; ++t) sl[t] = sl[t + 1];
             sl[5] = sl[0]; // ring5(kL) == ring5(kL - 5)
-            // ---- load + primitives of plane kL on R2 ----
+            const int kG = kL - 2;
+            const int gkG = gidx(kG, nk, pk);
+            const bool g_act = kG >= k0 - 1 && gkG >= 0 && col_ok;
+            const int rG = ring2(kG);
+            // ---- static fields of plane kG (R1, this thread's column) and
+            //      load + primitives of plane kL on R2 ----
+            float m[9], csd2 = 0.0f, rjG = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int t = 0; t < 9; ++t) m[t] = 0.0f;
+            if (g_act) {
+                const long long o = gkG * plane + ocol;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) m[t] = M[t * fs + o];
+                const float jinv = M[MET_JINV * fs + o];
+                csd2 = M[MET_CSD2 * fs + o];
+                rjG = M[MET_J * fs + o];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) nrm[a] = M[(MET_NORM + a) * fs + o];
+                S.MA[(rG * 2 + 0) * N1 + c1] = make_float4(m[0], m[1], m[2], m[3]);
+                S.MA[(rG * 2 + 1) * N1 + c1] = make_float4(m[4], m[5], m[6], m[7]);
+                S.MB[rG * N1 + c1] = make_float2(m[8], jinv);
+            }
             {
                 const int gk = gidx(kL, nk, pk);
                 if (gk >= 0) {
-                    float *slot = SP + sl[5] * PSLOT;
+                    const int sb = sl[5] * N2;
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
                         if (lc[t] < 0) continue;
@@ -278,129 +399,76 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                         const float u = Qs[fs + o] * rrj, v = Qs[2 * fs + o] * rrj, w = Qs[3 * fs + o] * rrj;
                         const float e = Qs[4 * fs + o] * rj;
                         const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
-                        const int c = lc[t];
-                        slot[c] = rho;
-                        slot[N2 + c] = u;
-                        slot[2 * N2 + c] = v;
-                        slot[3 * N2 + c] = w;
-                        slot[4 * N2 + c] = p;
-                        slot[5 * N2 + c] = FP.gam * p * rr;
+                        S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
+                        S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
                     }
                 }
             }
             __syncthreads();
-            // ---- derivatives, SGS, sensors, lambda-bar of plane kG = kL - 2 on R1 (one cell per thread) ----
-            const int kG = kL - 2;
-            {
-                const int gk = gidx(kG, nk, pk);
-                if (kG >= k0 - 1 && gk >= 0 && col_ok) {
-                    float *sg = SG + ring2(kG) * NGF * N1;
-                    float *sm = SM + ring2(kG) * NMF * N1;
-                    const long long o = gk * plane + ocol;
-                    float m[9];
+            // ---- derivatives, SGS, sensors, lambda-bar of plane kG on R1 (one cell per thread) ----
+            if (g_act) {
+                const int s0 = sl[3] * N2 + c2; // plane kG
+                const float4 A0 = S.PA[s0];
+                const float2 B0 = S.PB[s0];
+                D3 dd[3];
 #pragma unroll
-                    for (int t = 0; t < 9; ++t) {
-                        m[t] = M[t * fs + o];
-                        sm[t * N1 + c1] = m[t];
+                for (int a = 0; a < 2; ++a) {
+                    const int st = a == 0 ? 1 : C2X;
+                    const int tt = a == 0 ? ti : tj;
+                    if (tt == 0) {
+                        dd[a] = deriv_central(S.PA[s0 - st], S.PB[s0 - st], B0.x, S.PA[s0 + st], S.PB[s0 + st]);
+                    } else {
+                        const int o1 = s0 + (tt - 1) * st, o2 = s0 + tt * st, o3 = s0 + (tt + 1) * st;
+                        dd[a] = deriv_end(tt, S.PA[o1], S.PB[o1], S.PA[o2], S.PB[o2], S.PA[o3], S.PB[o3]);
                     }
-                    const float jinv = M[MET_JINV * fs + o];
-                    const float csd2 = M[MET_CSD2 * fs + o];
-                    sm[9 * N1 + c1] = jinv;
-                    // zeta stencil of this plane (uniform): central, or one-sided at an end
-                    const int tk = (!pk && gk == 0) ? 1 : ((!pk && gk == nk - 1) ? -1 : 0);
-                    const float *P0 = SP + sl[3] * PSLOT; // plane kG
-                    float d[4][3];
-                    const int pf[4] = {1, 2, 3, 5};
-                    // xi and eta derivatives from the plane-kG slot
-#pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        const int st = a == 0 ? 1 : C2X;
-                        const int tt = a == 0 ? ti : tj;
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            const float *Fp = P0 + pf[f] * N2 + c2;
-                            float acc;
-                            if (tt == 0) acc = 0.5f * (Fp[st] - Fp[-st]);
-                            else if (tt > 0) acc = -1.5f * Fp[0] + 2.0f * Fp[st] - 0.5f * Fp[2 * st];
-                            else acc = 1.5f * Fp[0] - 2.0f * Fp[-st] + 0.5f * Fp[-2 * st];
-                            d[f][a] = acc;
-                        }
-                    }
-                    {
-                        const float *Pm2 = SP + sl[1] * PSLOT, *Pm1 = SP + sl[2] * PSLOT;
-                        const float *Pp1 = SP + sl[4] * PSLOT, *Pp2 = SP + sl[5] * PSLOT;
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            const int o2 = pf[f] * N2 + c2;
-                            float acc;
-                            if (tk == 0) acc = 0.5f * (Pp1[o2] - Pm1[o2]);
-                            else if (tk > 0) acc = -1.5f * P0[o2] + 2.0f * Pp1[o2] - 0.5f * Pp2[o2];
-                            else acc = 1.5f * P0[o2] - 2.0f * Pm1[o2] + 0.5f * Pm2[o2];
-                            d[f][2] = acc;
-                        }
-                    }
-                    // pressure sensors; an end point uses its interior neighbour's
-                    float nu[3];
-                    {
-                        const float *Pp = P0 + 4 * N2 + c2;
-#pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const int st = a == 0 ? 1 : C2X;
-                            const int off = (a == 0 ? ti : tj) * st;
-                            const float pm = Pp[off - st], p0 = Pp[off], pp = Pp[off + st];
-                            nu[a] = fabsf(pp - 2.0f * p0 + pm) / (pp + 2.0f * p0 + pm);
-                        }
-                        const float *Qm, *Q0, *Qp;
-                        if (tk == 0) { Qm = SP + sl[2] * PSLOT; Q0 = P0; Qp = SP + sl[4] * PSLOT; }
-                        else if (tk > 0) { Qm = P0; Q0 = SP + sl[4] * PSLOT; Qp = SP + sl[5] * PSLOT; }
-                        else { Qm = SP + sl[1] * PSLOT; Q0 = SP + sl[2] * PSLOT; Qp = P0; }
-                        const int o4 = 4 * N2 + c2;
-                        const float pm = Qm[o4], p0 = Q0[o4], pp = Qp[o4];
-                        nu[2] = fabsf(pp - 2.0f * p0 + pm) / (pp + 2.0f * p0 + pm);
-                    }
-                    const float rj = 1.0f / jinv;
-                    float gu[3][3];
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc)
-                            gu[i][cc] = (m[cc] * d[i][0] + m[3 + cc] * d[i][1] + m[6 + cc] * d[i][2]) * rj;
-                    float ss = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        ss += gu[i][i] * gu[i][i];
-#pragma unroll
-                        for (int cc = i + 1; cc < 3; ++cc) {
-                            const float sic = 0.5f * (gu[i][cc] + gu[cc][i]);
-                            ss += 2.0f * sic * sic;
-                        }
-                    }
-                    const float rho = P0[c2], u = P0[N2 + c2], v = P0[2 * N2 + c2], w = P0[3 * N2 + c2],
-                                T = P0[5 * N2 + c2];
-                    const float mus = rho * csd2 * sqrtf(2.0f * ss);
-                    const float sT = sqrtf(T);
-                    const float mu = T * sT * FP.suth1 / (T + FP.suthS);
-#pragma unroll
-                    for (int f = 0; f < 4; ++f)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) sg[(3 * f + a) * N1 + c1] = d[f][a];
-                    sg[GF_MUEFF * N1 + c1] = mu * FP.inv_Re + mus;
-                    sg[GF_KAP * N1 + c1] = mu * FP.kap_mol + mus * FP.kap_sgs;
-                    float lam[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        sg[(GF_NU + a) * N1 + c1] = nu[a];
-                        const float JU = m[3 * a] * u + m[3 * a + 1] * v + m[3 * a + 2] * w;
-                        const float nrm = sqrtf(m[3 * a] * m[3 * a] + m[3 * a + 1] * m[3 * a + 1] +
-                                                m[3 * a + 2] * m[3 * a + 2]);
-                        lam[a] = (fabsf(JU) + sT * nrm) * rj;
-                    }
-                    const float s01 = sqrtf(lam[0] * lam[1]), s02 = sqrtf(lam[0] * lam[2]),
-                                s12 = sqrtf(lam[1] * lam[2]);
-                    sg[(GF_LAM + 0) * N1 + c1] = lam[0] + s01 + s02;
-                    sg[(GF_LAM + 1) * N1 + c1] = lam[1] + s01 + s12;
-                    sg[(GF_LAM + 2) * N1 + c1] = lam[2] + s02 + s12;
                 }
+                {
+                    // zeta stencil of this plane (uniform): central, or one-sided at an end
+                    const int tk = (!pk && gkG == 0) ? 1 : ((!pk && gkG == nk - 1) ? -1 : 0);
+                    if (tk == 0) {
+                        const int om = sl[2] * N2 + c2, op = sl[4] * N2 + c2;
+                        dd[2] = deriv_central(S.PA[om], S.PB[om], B0.x, S.PA[op], S.PB[op]);
+                    } else {
+                        const int o1 = sl[tk > 0 ? 3 : 1] * N2 + c2, o2 = sl[tk > 0 ? 4 : 2] * N2 + c2,
+                                  o3 = sl[tk > 0 ? 5 : 3] * N2 + c2;
+                        dd[2] = deriv_end(tk, S.PA[o1], S.PB[o1], S.PA[o2], S.PB[o2], S.PA[o3], S.PB[o3]);
+                    }
+                }
+                // physical velocity gradient by the chain rule, |S|, Smagorinsky mu_sgs
+                float gu[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        gu[i][cc] = (m[cc] * cmp(dd[0].d, i) + m[3 + cc] * cmp(dd[1].d, i) +
+                                     m[6 + cc] * cmp(dd[2].d, i)) * rjG;
+                float ss = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    ss += gu[i][i] * gu[i][i];
+#pragma unroll
+                    for (int cc = i + 1; cc < 3; ++cc) {
+                        const float sic = 0.5f * (gu[i][cc] + gu[cc][i]);
+                        ss += 2.0f * sic * sic;
+                    }
+                }
+                const float rho = A0.x, T = B0.y;
+                const float mus = rho * csd2 * sqrtf(2.0f * ss);
+                const float sT = sqrt_pos(T);
+                const float mu = __fdividef(T * sT * FP.suth1, T + FP.suthS);
+                float lam[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float JU = m[3 * a] * A0.y + m[3 * a + 1] * A0.z + m[3 * a + 2] * A0.w;
+                    lam[a] = (fabsf(JU) + sT * nrm[a]) * rjG;
+                }
+                const float s01 = sqrt_pos(lam[0] * lam[1]), s02 = sqrt_pos(lam[0] * lam[2]),
+                            s12 = sqrt_pos(lam[1] * lam[2]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) S.GD[(rG * 3 + a) * N1 + c1] = dd[a].d;
+                S.GC[(rG * 2 + 0) * N1 + c1] = make_float4(mu * FP.inv_Re + mus, mu * FP.kap_mol + mus * FP.kap_sgs,
+                                                           dd[0].nu, lam[0] + s01 + s02);
+                S.GC[(rG * 2 + 1) * N1 + c1] = make_float4(dd[1].nu, lam[1] + s01 + s12, dd[2].nu, lam[2] + s02 + s12);
             }
             __syncthreads();
             // ---- interfaces and update of plane kU = kL - 3 ----
@@ -408,52 +476,84 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             if (kU >= k0 - 1) {
                 const int gk = gidx(kU, nk, pk);
                 const bool plane_ok = gk >= 0;
-                const int sU = sl[2] * PSLOT;
-                const int g0 = ring2(kU) * NGF * N1, gm0 = ring2(kU) * NMF * N1;
-                float hx[5] = {0, 0, 0, 0, 0}, hy[5] = {0, 0, 0, 0, 0}, hz[5] = {0, 0, 0, 0, 0};
                 const bool first = kU == k0 - 1; // only the -1/2 zeta flux of the chunk
-                if (!first && plane_ok && xi_ok) {
-                    const bool lo = !pi && gi == 0, hi = !pi && gi + 1 == ni - 1;
-                    fused_iface<0, TY>(S, FP, sU + c2 - 1, sU + c2, sU + c2 + 1, sU + c2 + 2, g0 + c1, g0 + c1 + 1,
-                                       gm0 + c1, gm0 + c1 + 1, lo, hi, hx);
+                const bool do_xi = !first && plane_ok && xi_ok;
+                const bool do_eta = !first && plane_ok && eta_ok;
+                const bool do_zeta = plane_ok && out_col && (pk || gk < nk - 1);
+                const bool upd = !first && plane_ok && out_col && kU < k1;
+                const long long o = (long long)(plane_ok ? gk : 0) * plane + ocol;
+                const int rU = ring2(kU), sU = sl[2] * N2;
+                OwnPt L;
+                if (do_xi || do_eta || do_zeta) {
+                    L.a = S.PA[sU + c2];
+                    {
+                        const float2 b = S.PB[sU + c2];
+                        L.p = b.x;
+                        L.T = b.y;
+                    }
+                    {
+                        const float4 u0 = S.MA[(rU * 2 + 0) * N1 + c1], u1 = S.MA[(rU * 2 + 1) * N1 + c1];
+                        const float2 u2 = S.MB[rU * N1 + c1];
+                        L.m[0] = u0.x; L.m[1] = u0.y; L.m[2] = u0.z; L.m[3] = u0.w;
+                        L.m[4] = u1.x; L.m[5] = u1.y; L.m[6] = u1.z; L.m[7] = u1.w;
+                        L.m[8] = u2.x;
+                        L.jinv = u2.y;
+                    }
+                    L.c1 = c1;
+                    L.pl = rU;
                 }
-                if (!first && plane_ok && eta_ok) {
-                    const bool lo = !pj && gj == 0, hi = !pj && gj + 1 == nj - 1;
-                    fused_iface<1, TY>(S, FP, sU + c2 - C2X, sU + c2, sU + c2 + C2X, sU + c2 + 2 * C2X, g0 + c1,
-                                       g0 + c1 + FX, gm0 + c1, gm0 + c1 + FX, lo, hi, hy);
-                }
-                if (plane_ok && out_col && (pk || gk < nk - 1)) {
-                    const bool lo = !pk && gk == 0, hi = !pk && gk + 1 == nk - 1;
-                    fused_iface<2, TY>(S, FP, sl[1] * PSLOT + c2, sU + c2, sl[3] * PSLOT + c2, sl[4] * PSLOT + c2,
-                                       g0 + c1, ring2(kU + 1) * NGF * N1 + c1, gm0 + c1,
-                                       ring2(kU + 1) * NMF * N1 + c1, lo, hi, hz);
-                }
-                float hxm[5];
+                // residual R = sum over axes of (flux(+1/2) - flux(-1/2)); the
+                // -1/2 xi flux comes from the lane below, the -1/2 zeta flux
+                // from the previous plane, the -1/2 eta flux (row below)
+                // through shared memory after the barrier
+                float R[5], hy[5] = {0, 0, 0, 0, 0};
+                {
+                    float hx[5] = {0, 0, 0, 0, 0};
+                    if (do_xi)
+                        fused_iface<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU, xi_lo,
+                                           xi_hi, hx);
 #pragma unroll
-                for (int f = 0; f < 5; ++f) {
-                    hxm[f] = __shfl_up_sync(0xffffffffu, hx[f], 1);
-                    SH[(f * TY + ty) * FX + tx] = hy[f];
+                    for (int f = 0; f < 5; ++f) R[f] = hx[f] - __shfl_up_sync(0xffffffffu, hx[f], 1);
+                }
+                if (do_eta)
+                    fused_iface<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX, rU,
+                                       eta_lo, eta_hi, hy);
+#pragma unroll
+                for (int f = 0; f < 5; ++f) S.SH[(f * TY + ty) * FX + tx] = hy[f];
+                {
+                    float hz[5] = {0, 0, 0, 0, 0};
+                    if (do_zeta) {
+                        const bool lo = !pk && gk == 0, hi = !pk && gk + 1 == nk - 1;
+                        fused_iface<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
+                                           ring2(kU + 1), lo, hi, hz);
+                    }
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) {
+                        R[f] += hz[f] - hz_prev[f];
+                        hz_prev[f] = hz[f];
+                    }
+                }
+                // Q(0) of the updated point, requested before the exchange barrier
+                float q0v[5] = {0, 0, 0, 0, 0};
+                if (upd && !rhs_only) {
+                    const float *Q0 = J.q[0];
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) q0v[f] = Q0[f * fs + o];
                 }
                 __syncthreads();
-                if (!first && plane_ok && out_col && kU < k1) {
-                    const long long o = gk * plane + ocol;
-                    float R[5];
+                if (upd) {
 #pragma unroll
-                    for (int f = 0; f < 5; ++f)
-                        R[f] = (hx[f] - hxm[f]) + (hy[f] - SH[(f * TY + ty - 1) * FX + tx]) + (hz[f] - hz_prev[f]);
+                    for (int f = 0; f < 5; ++f) R[f] += hy[f] - S.SH[(f * TY + ty - 1) * FX + tx];
                     if (rhs_only) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) J.rhs[f * fs + o] = R[f];
                     } else {
                         const float adt = c_alpha_f[stage] * (float)dt[jet];
-                        const float *Q0 = J.q[0];
                         float *Qd = J.q[dst];
 #pragma unroll
-                        for (int f = 0; f < 5; ++f) Qd[f * fs + o] = Q0[f * fs + o] - adt * R[f];
+                        for (int f = 0; f < 5; ++f) Qd[f * fs + o] = q0v[f] - adt * R[f];
                     }
                 }
-#pragma unroll
-                for (int f = 0; f < 5; ++f) hz_prev[f] = hz[f];
             }
             __syncthreads();
         }
