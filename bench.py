@@ -35,7 +35,9 @@ from paper_2212_12365_gb300 import inputs as I  # noqa: E402
 FLOPS_PER_PT_STAGE = {"point": 96, "grads": 141, "iface": 765, "update": 41}
 # Algorithmic HBM bytes per point and stage: stages 2-5 read Q(l-1), Q(0) and 10
 # metric values and write Q(l); stage 1 reads Q(0) once: 24 values on average.
-ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4}
+ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
+                           # separable metrics (product grids): no 3-D metric fields, 14 values
+                           "fp32-sep": 14 * 4}
 # DRAM bytes per point of one launch of the dominant kernel, from the ncu
 # captures summarised in profiles/ (None once the kernel changed since).
 TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 871.0, ("fp32", "k_fused"): 92.4}
@@ -202,13 +204,14 @@ def precision_form(args, spec, fp, les, torch, fp64_value):
     """FP32 storage/arithmetic on the same grid (metrics and sums in FP64): its
     rate, speedup over the FP64 path, and relative L2 per field against the FP64
     path after the same number of steps from the ambient start."""
-    out = {}
+    forms = {}
     states = {}
     steps = args.warmup + args.steps
-    for prec in (les.LES_FP32, les.LES_FP64):
+    names = {les.LES_FP32: "fp32", les.LES_FP32_SEPARABLE: "fp32-sep"}
+    for prec in (les.LES_FP32, les.LES_FP32_SEPARABLE, les.LES_FP64):
         s = les.Solver(spec, fp, prec)
         s.set_state(I.ambient_primitives(spec.N, fp.TR), les.LES_STATE_PRIMITIVE)
-        if prec == les.LES_FP32:
+        if prec != les.LES_FP64:
             s.step(args.warmup)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -218,19 +221,24 @@ def precision_form(args, spec, fp, les, torch, fp64_value):
             e1.record(st)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-            out = {"precision": "fp32", "value": spec.N * 5 * args.steps / (ms / 1e3),
-                   "ms_per_step": ms / args.steps, "stage": les.les_describe(s.h)}
+            forms[prec] = {"precision": names[prec], "value": spec.N * 5 * args.steps / (ms / 1e3),
+                           "ms_per_step": ms / args.steps, "stage": les.les_describe(s.h)}
         else:
             s.step(steps)
         states[prec] = s.get_state(les.LES_STATE_CONSERVED)
         s.close()
-    a, b = states[les.LES_FP32], states[les.LES_FP64]
-    err = np.sqrt(((a - b) ** 2).sum(axis=1) / np.maximum((b ** 2).sum(axis=1), 1e-300))
-    out["speedup_vs_fp64"] = out["value"] / fp64_value
-    out["rel_l2_vs_fp64_per_field"] = [float(e) for e in err]
-    out["after_steps"] = steps
-    out["hbm_frac_algorithmic"] = out["value"] * ALGO_BYTES_PER_PT_STAGE["fp32"] / 1e9 / \
-        measured_peaks().get("hbm_gbs", 6750.0)
+    b = states[les.LES_FP64]
+    for prec, f in forms.items():
+        a = states[prec]
+        err = np.sqrt(((a - b) ** 2).sum(axis=1) / np.maximum((b ** 2).sum(axis=1), 1e-300))
+        f["speedup_vs_fp64"] = f["value"] / fp64_value
+        f["rel_l2_vs_fp64_per_field"] = [float(e) for e in err]
+        f["after_steps"] = steps
+        f["hbm_frac_algorithmic"] = f["value"] * ALGO_BYTES_PER_PT_STAGE[names[prec]] / 1e9 / \
+            measured_peaks().get("hbm_gbs", 6750.0)
+    out = forms[les.LES_FP32]
+    # the separable-metric stage (Cartesian-product grids only), reported apart
+    out["separable"] = forms[les.LES_FP32_SEPARABLE]
     return out
 
 
@@ -247,7 +255,7 @@ def run_ours(args):
     build.build()
     make, prec_default = WORKLOADS[args.workload]
     prec = args.precision or prec_default
-    P = les.LES_FP64 if prec == "fp64" else les.LES_FP32
+    P = {"fp64": les.LES_FP64, "fp32": les.LES_FP32, "fp32-sep": les.LES_FP32_SEPARABLE}[prec]
     spec, fp = make()
     batch = isinstance(spec, list)
     specs = spec if batch else [spec]
@@ -305,7 +313,8 @@ def run_ours(args):
     bytes_pt_stage = ALGO_BYTES_PER_PT_STAGE[prec]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_pt * N if traffic_pt else None,
-                "peak_source": f"nominal {prec.upper()} unit count x 2.07 GHz (not in MEASURED_PEAKS.json)",
+                "peak_source": f"nominal {'FP64' if prec == 'fp64' else 'FP32'} unit count x 2.07 GHz "
+                               "(not in MEASURED_PEAKS.json)",
                 "flops_per_point_stage": flops_pt,
                 "share": prof[dom][0] / tot if tot else None,
                 "per_kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
@@ -376,7 +385,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jet-384x256x144", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp32-sep"],
+                    help="fp32-sep: FP32 with the separable-metric stage (product grids)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 line of the FP64 default run")

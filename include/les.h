@@ -61,6 +61,13 @@ extern "C" {
  * Jacobian are always computed in FP64; diagnostics sum in FP64. */
 #define LES_FP64 0
 #define LES_FP32 1
+/* FP32 with the separable-metric stage: only for a Cartesian-product grid
+ * (x depends on i only, y on j only, z on k only; LES_ERR_ARG otherwise).
+ * The cofactors are then diagonal products of the three 1-D spacings
+ * dx/dxi, dy/deta, dz/dzeta (Sec. "Transformation of Coordinates"), which the
+ * stage kernel reads from three 1-D tables instead of nine stored fields;
+ * everything else behaves as LES_FP32 (state kinds, probe, diagnostics). */
+#define LES_FP32_SEPARABLE 2
 
 /* State kinds for les_set_state / les_get_state. */
 #define LES_STATE_CONSERVED 0 /* unscaled Q = [rho, rho u, rho v, rho w, e] */
@@ -242,6 +249,10 @@ int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints
  * on the handle. */
 const char *les_describe(les_handle *h);
 
+/* Text of the last error of handle h; with h = NULL, the text of the last
+ * failed les_create_grid / les_create_batch of the calling thread ("" if
+ * none).  The pointer stays valid until the next call on the handle (or the
+ * next creation on the thread). */
 const char *les_last_error(les_handle *h);
 int les_destroy(les_handle *h);
 

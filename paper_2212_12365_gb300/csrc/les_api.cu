@@ -32,6 +32,7 @@ struct JetHost {
     // device pointers (typed as bytes; the element type follows the precision)
     char *met, *q[3], *prim, *grad, *hflux, *rhs;
     double *jinv64, *inflow_r;
+    float4 *h1[3];                     // FP32: 1-D spacings of a product grid (separable form)
     int nblk_pt, nblk_bc[3];
 };
 
@@ -42,7 +43,8 @@ constexpr int DIAG_BLOCKS = 608; // blocks of the diagnostics reduction (fixed o
 } // namespace
 
 struct les_handle {
-    int prec = LES_FP64;
+    int prec = LES_FP64;        // LES_FP64 or LES_FP32 (storage and arithmetic)
+    bool sep = false;           // FP32 separable-metric stage (LES_FP32_SEPARABLE)
     int njets = 0;
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;
@@ -95,6 +97,10 @@ struct les_handle {
         }                                                                                          \
     } while (0)
 
+// Text of the last failed les_create_grid / les_create_batch of this thread
+// (returned by les_last_error(NULL)).
+static thread_local std::string g_create_err;
+
 static int fail(les_handle *h, int code, const std::string &msg)
 {
     if (h) h->err = msg;
@@ -110,7 +116,8 @@ static std::string validate(const les_grid_desc *g, const les_params *p)
     if (!g || !p) return "null descriptor or parameters";
     if (g->ni < 4 || g->nj < 4 || g->nk < 4) return "each axis needs >= 4 points";
     if (!g->x || !g->y || !g->z) return "null coordinate array";
-    if (g->precision != LES_FP64 && g->precision != LES_FP32) return "unknown precision";
+    if (g->precision != LES_FP64 && g->precision != LES_FP32 && g->precision != LES_FP32_SEPARABLE)
+        return "unknown precision";
     for (int a = 0; a < 3; ++a) {
         bool pf = g->face_bc[2 * a] == LES_BC_PERIODIC, pb = g->face_bc[2 * a + 1] == LES_BC_PERIODIC;
         if (g->periodic[a] != 0 && g->periodic[a] != 1) return "periodic flags must be 0/1";
@@ -159,6 +166,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     size_t o_hf = take(NHF * fb);
     size_t o_rhs = take(NF * fb);
     size_t o_inr = take((size_t)g->nj * g->nk * 8);
+    size_t o_h1 = prec == LES_FP32 ? take((size_t)(g->ni + g->nj + g->nk) * 16) : 0;
     J.bytes = off;
     // store offsets relative to the jet region in the pointers for now
     J.met = (char *)o_met;
@@ -171,7 +179,13 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     J.hflux = (char *)o_hf;
     J.rhs = (char *)o_rhs;
     J.inflow_r = (double *)o_inr;
+    J.h1[0] = prec == LES_FP32 ? (float4 *)o_h1 : nullptr;
+    J.h1[1] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)g->ni * 16) : nullptr;
+    J.h1[2] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)(g->ni + g->nj) * 16) : nullptr;
 }
+
+// Storage precision of a descriptor's precision code.
+static int storage_prec(int precision) { return precision == LES_FP64 ? LES_FP64 : LES_FP32; }
 
 struct GlobalPlan {
     size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, total;
@@ -206,7 +220,7 @@ extern "C" size_t les_workspace_bytes(const les_grid_desc *g)
 {
     if (!g || g->ni < 4 || g->nj < 4 || g->nk < 4) return 0;
     JetHost J;
-    plan_jet(g, g->precision, J);
+    plan_jet(g, storage_prec(g->precision), J);
     size_t jd = g->precision == LES_FP64 ? jetdev_size<double>() : jetdev_size<float>();
     GlobalPlan P = plan_global(1, jd, DIAG_BLOCKS, J.N);
     return align_up(P.total, 256) + J.bytes;
@@ -273,6 +287,10 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
     CK(cudaGetLastError());
     Launch<real>::static_fields(met64, J.fs, J.pitch, J.n, J.per, h->prec == LES_FP64 ? 1 : 0, h->st);
     CK(cudaGetLastError());
+    if (h->sep) {
+        launch_sep_metrics(dx, dy, dz, J.n, J.per, J.shift, J.h1[0], J.h1[1], J.h1[2], h->st);
+        CK(cudaGetLastError());
+    }
     if (h->prec == LES_FP32) {
         Launch<real>::convert_metrics(met64, J.fs, (real *)J.met, J.fs, J.npad, h->st);
         CK(cudaGetLastError());
@@ -308,6 +326,8 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
             g->z[p] != g->z[k * (size_t)J.n[0] * J.n[1]])
             J.product = false;
     }
+    if (h->sep && !J.product)
+        return fail(h, LES_ERR_ARG, "LES_FP32_SEPARABLE needs a Cartesian-product grid x(i), y(j), z(k)");
     if (J.product) {
         for (int i = 0; i < J.n[0]; ++i) J.ax[0].push_back(g->x[i]);
         for (int j = 0; j < J.n[1]; ++j) J.ax[1].push_back(g->y[(size_t)j * J.n[0]]);
@@ -357,9 +377,9 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     const int grid = std::max(1, std::min(items, h->nsm * (h->fused_ty == 16 ? 1 : 2)));
     if (jet >= 0) jets += jet;
     if (h->fused_ty == 16)
-        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, st);
+        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, st);
     else
-        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, st);
+        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, st);
 }
 
 template <typename real>
@@ -367,10 +387,12 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
                        les_handle **out)
 {
     les_handle *h = new les_handle();
-    h->prec = g[0].precision;
+    h->prec = storage_prec(g[0].precision);
+    h->sep = g[0].precision == LES_FP32_SEPARABLE;
     h->njets = njets;
     h->st = (cudaStream_t)stream;
     auto bail = [&](int code) {
+        g_create_err = h->err;
         les_destroy(h);
         *out = nullptr;
         return code;
@@ -445,6 +467,8 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
         J.hflux = jb + (size_t)J.hflux;
         J.rhs = jb + (size_t)J.rhs;
         J.inflow_r = (double *)(jb + (size_t)J.inflow_r);
+        for (int a = 0; a < 3; ++a)
+            if (J.h1[a]) J.h1[a] = (float4 *)(jb + (size_t)J.h1[a]);
     }
     for (int j = 0; j < njets; ++j) {
         int rc = setup_jet<real>(h, h->J[j], &g[j]);
@@ -472,6 +496,8 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             const double S = pp.S1_dim / (pp.TR * pp.T_inf_dim);
             F.suth1 = (float)(1.0 + S);
             F.suthS = (float)S;
+            F.cs2 = (float)(pp.Cs * pp.Cs);
+            for (int a = 0; a < 3; ++a) h->fj[j].h1[a] = h->J[j].h1[a];
         }
         int rc = set_fused_tiling(h, 8, 32);
         if (rc) return bail(rc);
@@ -517,16 +543,26 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
 static int create_any(const les_grid_desc *g, const les_params *p, int njets, void *stream,
                       les_handle **out)
 {
-    if (!out) return LES_ERR_ARG;
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "null output pointer";
+        return LES_ERR_ARG;
+    }
     *out = nullptr;
-    if (!g || !p || njets < 1) return LES_ERR_ARG;
+    if (!g || !p || njets < 1) {
+        g_create_err = "null descriptor or parameters, or njets < 1";
+        return LES_ERR_ARG;
+    }
     for (int j = 0; j < njets; ++j) {
         std::string msg = validate(&g[j], &p[j]);
         if (!msg.empty()) {
-            std::fprintf(stderr, "les_create: jet %d: %s\n", j, msg.c_str());
+            g_create_err = "jet " + std::to_string(j) + ": " + msg;
             return LES_ERR_ARG;
         }
-        if (g[j].precision != g[0].precision) return LES_ERR_ARG;
+        if (g[j].precision != g[0].precision) {
+            g_create_err = "all jets of a batch need the same precision";
+            return LES_ERR_ARG;
+        }
     }
     if (g[0].precision == LES_FP64) return create_impl<double>(g, p, njets, stream, out);
     return create_impl<float>(g, p, njets, stream, out);
@@ -868,7 +904,7 @@ static int autotune_fused(les_handle *h)
     std::string key;
     for (auto &J : h->J)
         key += std::to_string(J.n[0]) + "x" + std::to_string(J.n[1]) + "x" + std::to_string(J.n[2]) + "p" +
-               std::to_string(J.per[0] * 4 + J.per[1] * 2 + J.per[2]) + ";";
+               std::to_string(J.per[0] * 4 + J.per[1] * 2 + J.per[2]) + (h->sep ? "s;" : ";");
     auto it = g_tune_cache.find(key);
     if (it == g_tune_cache.end()) {
         const int tys[2] = {16, 8};
@@ -1057,7 +1093,7 @@ extern "C" int les_probe_frames(les_handle *h, int64_t *frames)
 
 extern "C" int64_t les_last_launch_count(les_handle *h) { return h ? h->last_launches : 0; }
 
-extern "C" const char *les_last_error(les_handle *h) { return h ? h->err.c_str() : "null handle"; }
+extern "C" const char *les_last_error(les_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 extern "C" const char *les_describe(les_handle *h)
 {
@@ -1066,7 +1102,7 @@ extern "C" const char *les_describe(les_handle *h)
     d = std::string(h->prec == LES_FP64 ? "fp64" : "fp32") + " jets=" + std::to_string(h->njets) +
         " device_bytes=" + std::to_string(h->bytes) + " stage=" +
         (h->prec == LES_FP64 ? std::string("point+grads+iface+update")
-                             : std::string("fused ") + (h->tuned ? h->tune_note : "ty=" + std::to_string(h->fused_ty) + " (untuned)")) +
+                             : std::string(h->sep ? "fused separable " : "fused ") + (h->tuned ? h->tune_note : "ty=" + std::to_string(h->fused_ty) + " (untuned)")) +
         " launches_per_step=" + std::to_string(h->launches_per_step);
     return d.c_str();
 }

@@ -48,6 +48,8 @@ __constant__ float c_alpha_f[5] = {0.25f, 1.0f / 6.0f, 0.375f, 0.5f, 1.0f};
 //   PB [5][NC2] float2  p T              (point ring)
 //   MB [2][NC1] float2  m8, J^-1
 //   SH [5][TY][FX] float  eta-interface fluxes of the current plane
+//   HX [C2X], HY [C2Y] float4  separable form: (h, 1/h, h^(2/3), 0) of the
+//                              tile's columns / rows, h = dx/dxi resp. dy/deta
 template <int TY> struct Geo {
     static constexpr int NT = FX * TY;
     static constexpr int C2X = FX + 2, C2Y = TY + 2, NC2 = C2X * C2Y; // R2: cells [-1, FX] x [-1, TY]
@@ -59,17 +61,21 @@ template <int TY> struct Geo {
     static constexpr size_t O_PB = O_MA + 16ull * 2 * 2 * NC1;
     static constexpr size_t O_MB = O_PB + 8ull * 5 * NC2;
     static constexpr size_t O_SH = O_MB + 8ull * 2 * NC1;
-    static constexpr size_t BYTES = O_SH + 4ull * 5 * TY * FX;
+    static constexpr size_t O_HX = O_SH + 4ull * 5 * TY * FX;
+    static constexpr size_t O_HY = O_HX + 16ull * C2X;
+    static constexpr size_t BYTES = O_HY + 16ull * C2Y;
 };
 
 template <int TY> struct Sm {
     float4 *PA, *GD, *GC, *MA;
     float2 *PB, *MB;
     float *SH;
+    float4 *HX, *HY;
     __device__ __forceinline__ explicit Sm(unsigned char *b)
         : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
           GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
-          PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH))
+          PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH)),
+          HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY))
     {
     }
 };
@@ -239,6 +245,103 @@ __device__ __forceinline__ void fused_iface(const Sm<TY> &S, const FusedParams &
     }
 }
 
+// Separable form of fused_iface on a Cartesian-product grid x = x(i),
+// y = y(j), z = z(k) (Sec. "Transformation of Coordinates" with diagonal
+// metrics): the cofactor matrix is diag(y_eta z_zeta, x_xi z_zeta,
+// x_xi y_eta), so the face factor of axis A is the product Sa of the two
+// tangential spacings (equal on both sides), J^-1 at the interface is
+// Sa * hb with hb the interface average of the spacing along A, and the
+// chain rule reduces to d/dx_c = (1/h_c) d/dxi_c.  hAL, hAR: spacing along A
+// at L and R; hT1/rhT1, hT2/rhT2: the tangential spacings and reciprocals
+// (axes B1 < B2).
+template <int A, int TY>
+__device__ __forceinline__ void fused_iface_sep(const Sm<TY> &S, const FusedParams &FP, const OwnPt &L, int r2,
+                                                int lm2, int rp2, int r1, int rpl, bool lo_end, bool hi_end,
+                                                float hAL, float hAR, float hT1, float rhT1, float hT2,
+                                                float rhT2, float H[5])
+{
+    constexpr int N1 = Geo<TY>::NC1;
+    const float hg = FP.hgam;
+    float LW[5];
+    wvec(L.a, L.p, hg, LW);
+    const float4 ra = S.PA[r2];
+    const float2 rb = S.PB[r2];
+    float WR[5], WLm[5], WRp[5];
+    wvec(ra, rb.x, hg, WR);
+    if (!lo_end) {
+        const float4 q = S.PA[lm2];
+        wvec(q, S.PB[lm2].x, hg, WLm);
+    }
+    if (!hi_end) {
+        const float4 q = S.PA[rp2];
+        wvec(q, S.PB[rp2].x, hg, WRp);
+    }
+    const float Sa = hT1 * hT2;
+    const float hb = 0.5f * (hAL + hAR);
+    const float jb = Sa * hb;
+    // centred inviscid flux: J^-1 U_A = Sa u_A on both sides
+    {
+        const float JUL = Sa * cmp(L.a, 1 + A), JUR = Sa * cmp(ra, 1 + A);
+#pragma unroll
+        for (int f = 0; f < 5; ++f) H[f] = 0.5f * (LW[f] * JUL + WR[f] * JUR);
+        H[1 + A] += 0.5f * Sa * (L.p + rb.x);
+    }
+    float mueL, kapL, nuL, lbL, mueR, kapR, nuR, lbR;
+    if (A == 0) {
+        const float4 c = S.GC[(L.pl * 2 + 0) * N1 + L.c1], d = S.GC[(rpl * 2 + 0) * N1 + r1];
+        mueL = c.x; kapL = c.y; nuL = c.z; lbL = c.w;
+        mueR = d.x; kapR = d.y; nuR = d.z; lbR = d.w;
+    } else {
+        const float2 c = *reinterpret_cast<const float2 *>(&S.GC[(L.pl * 2 + 0) * N1 + L.c1]);
+        const float2 e = reinterpret_cast<const float2 *>(&S.GC[(L.pl * 2 + 1) * N1 + L.c1])[A - 1];
+        const float2 d = *reinterpret_cast<const float2 *>(&S.GC[(rpl * 2 + 0) * N1 + r1]);
+        const float2 g = reinterpret_cast<const float2 *>(&S.GC[(rpl * 2 + 1) * N1 + r1])[A - 1];
+        mueL = c.x; kapL = c.y; nuL = e.x; lbL = e.y;
+        mueR = d.x; kapR = d.y; nuR = g.x; lbR = g.y;
+    }
+    // Turkel-Vatsa dissipation
+    {
+        const float eps2 = FP.k2 * fmaxf(nuL, nuR);
+        const float eps4 = fmaxf(0.0f, FP.k4 - eps2);
+        const float sc = jb * 0.5f * (lbL + lbR);
+        const float se2 = sc * eps2, se4 = sc * eps4;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            const float dW0 = WR[f] - LW[f];
+            const float dWp = hi_end ? -dW0 : WRp[f] - WR[f];
+            const float dWm = lo_end ? -dW0 : LW[f] - WLm[f];
+            const float d3 = dWp - 2.0f * dW0 + dWm;
+            H[f] -= se2 * dW0 - se4 * d3;
+        }
+    }
+    // compact viscous + SGS flux: only row A of the stress tensor is needed
+    {
+        const float rhb = 1.0f / hb;
+        constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
+        const float4 dR1 = S.GD[(rpl * 3 + B1) * N1 + r1], dR2 = S.GD[(rpl * 3 + B2) * N1 + r1];
+        const float4 dL1 = S.GD[(L.pl * 3 + B1) * N1 + L.c1], dL2 = S.GD[(L.pl * 3 + B2) * N1 + L.c1];
+        float gu[4][3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float lv = f == 0 ? L.a.y : (f == 1 ? L.a.z : (f == 2 ? L.a.w : L.T));
+            const float rv = f == 0 ? ra.y : (f == 1 ? ra.z : (f == 2 ? ra.w : rb.y));
+            gu[f][A] = (rv - lv) * rhb;
+            gu[f][B1] = 0.5f * (cmp(dL1, f) + cmp(dR1, f)) * rhT1;
+            gu[f][B2] = 0.5f * (cmp(dL2, f) + cmp(dR2, f)) * rhT2;
+        }
+        const float div3 = (gu[0][0] + gu[1][1] + gu[2][2]) * (1.0f / 3.0f);
+        const float coef = mueL + mueR;
+        const float kap = 0.5f * (kapL + kapR);
+        float tA[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tA[i] = i == A ? coef * (gu[A][A] - div3) : coef * 0.5f * (gu[A][i] + gu[i][A]);
+        const float vb0 = 0.5f * (L.a.y + ra.y), vb1 = 0.5f * (L.a.z + ra.z), vb2 = 0.5f * (L.a.w + ra.w);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) H[1 + i] -= Sa * tA[i];
+        H[4] -= Sa * (tA[0] * vb0 + tA[1] * vb1 + tA[2] * vb2 + kap * gu[3][A]);
+    }
+}
+
 // Derivative along one axis of (u, v, w, T) and the pressure sensor of the
 // point at ring offset 0, from the points at offsets -s, 0, +s (central) or,
 // at a non-periodic end, the one-sided second-order stencil (the sensor of
@@ -273,7 +376,7 @@ __device__ __forceinline__ D3 deriv_end(int t, const float4 &a1, const float2 &b
 
 } // namespace
 
-template <int TY>
+template <int TY, bool SEP>
 __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
             int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only)
@@ -350,6 +453,18 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
         }
+        if constexpr (SEP) {
+            // 1-D spacings of the tile's columns and rows (the previous item's
+            // last reads of HX/HY precede its final barrier)
+            if (tid < C2X) {
+                const int g = gidx(ib - 1 + tid, ni, pi);
+                S.HX[tid] = g >= 0 ? F.h1[0][g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else if (tid < C2X + G_::C2Y) {
+                const int t = tid - C2X;
+                const int g = gidx(jb - 1 + t, nj, pj);
+                S.HY[t] = g >= 0 ? F.h1[1][g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
         float hz_prev[5] = {0, 0, 0, 0, 0};
         // ring slots of planes kL-5 .. kL (sl[5] = plane kL); before the first
         // shift they describe the iteration before the first, kL = k0 - 4
@@ -358,6 +473,13 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         for (int t = 0; t < 6; ++t) sl[t] = ring5(k0 - 4 - 5 + t);
 
         __syncthreads(); // shared memory of the previous item is free
+        // separable form: J = 1/(hx hy hz) of the load-phase cells, in-plane part
+        float rJ2[2] = {0.0f, 0.0f};
+        if constexpr (SEP) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                if (lc[t] >= 0) rJ2[t] = S.HX[lc[t] % C2X].y * S.HY[lc[t] / C2X].y;
+        }
         for (int kL = k0 - 3; kL <= k1 + 2; ++kL) {
 #pragma unroll
             for (int t = 0; t < 5; ++t) sl[t] = sl[t + 1];
@@ -371,7 +493,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             float m[9], csd2 = 0.0f, rjG = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int t = 0; t < 9; ++t) m[t] = 0.0f;
-            if (g_act) {
+            if (!SEP && g_act) {
                 const long long o = gkG * plane + ocol;
 #pragma unroll
                 for (int t = 0; t < 9; ++t) m[t] = M[t * fs + o];
@@ -388,11 +510,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 const int gk = gidx(kL, nk, pk);
                 if (gk >= 0) {
                     const int sb = sl[5] * N2;
+                    const float rhzL = SEP ? F.h1[2][gk].y : 0.0f;
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
                         if (lc[t] < 0) continue;
                         const long long o = gk * plane + lo2[t];
-                        const float rj = M[MET_J * fs + o];
+                        const float rj = SEP ? rJ2[t] * rhzL : M[MET_J * fs + o];
                         const float rho = Qs[o] * rj;
                         const float rr = 1.0f / rho;
                         const float rrj = rj * rr;
@@ -436,12 +559,25 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
                 // physical velocity gradient by the chain rule, |S|, Smagorinsky mu_sgs
                 float gu[3][3];
+                float rh[3];
+                if constexpr (SEP) {
+                    const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gkG];
+                    rh[0] = hX.y;
+                    rh[1] = hY.y;
+                    rh[2] = hZ.y;
+                    csd2 = FP.cs2 * hX.z * hY.z * hZ.z;
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+                    for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
-                        gu[i][cc] = (m[cc] * cmp(dd[0].d, i) + m[3 + cc] * cmp(dd[1].d, i) +
-                                     m[6 + cc] * cmp(dd[2].d, i)) * rjG;
+                        for (int cc = 0; cc < 3; ++cc) gu[i][cc] = cmp(dd[cc].d, i) * rh[cc];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc)
+                            gu[i][cc] = (m[cc] * cmp(dd[0].d, i) + m[3 + cc] * cmp(dd[1].d, i) +
+                                         m[6 + cc] * cmp(dd[2].d, i)) * rjG;
+                }
                 float ss = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
@@ -459,8 +595,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 float lam[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float JU = m[3 * a] * A0.y + m[3 * a + 1] * A0.z + m[3 * a + 2] * A0.w;
-                    lam[a] = (fabsf(JU) + sT * nrm[a]) * rjG;
+                    if constexpr (SEP) {
+                        lam[a] = (fabsf(cmp(A0, 1 + a)) + sT) * fabsf(rh[a]);
+                    } else {
+                        const float JU = m[3 * a] * A0.y + m[3 * a + 1] * A0.z + m[3 * a + 2] * A0.w;
+                        lam[a] = (fabsf(JU) + sT * nrm[a]) * rjG;
+                    }
                 }
                 const float s01 = sqrt_pos(lam[0] * lam[1]), s02 = sqrt_pos(lam[0] * lam[2]),
                             s12 = sqrt_pos(lam[1] * lam[2]);
@@ -491,7 +631,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                         L.p = b.x;
                         L.T = b.y;
                     }
-                    {
+                    if constexpr (!SEP) {
                         const float4 u0 = S.MA[(rU * 2 + 0) * N1 + c1], u1 = S.MA[(rU * 2 + 1) * N1 + c1];
                         const float2 u2 = S.MB[rU * N1 + c1];
                         L.m[0] = u0.x; L.m[1] = u0.y; L.m[2] = u0.z; L.m[3] = u0.w;
@@ -509,23 +649,44 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 float R[5], hy[5] = {0, 0, 0, 0, 0};
                 {
                     float hx[5] = {0, 0, 0, 0, 0};
-                    if (do_xi)
-                        fused_iface<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU, xi_lo,
-                                           xi_hi, hx);
+                    if (do_xi) {
+                        if constexpr (SEP) {
+                            const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
+                            fused_iface_sep<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU,
+                                                   xi_lo, xi_hi, hX.x, S.HX[tx + 2].x, hY.x, hY.y, hZ.x, hZ.y, hx);
+                        } else {
+                            fused_iface<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU, xi_lo,
+                                               xi_hi, hx);
+                        }
+                    }
 #pragma unroll
                     for (int f = 0; f < 5; ++f) R[f] = hx[f] - __shfl_up_sync(0xffffffffu, hx[f], 1);
                 }
-                if (do_eta)
-                    fused_iface<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX, rU,
-                                       eta_lo, eta_hi, hy);
+                if (do_eta) {
+                    if constexpr (SEP) {
+                        const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
+                        fused_iface_sep<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX,
+                                               rU, eta_lo, eta_hi, hY.x, S.HY[ty + 2].x, hX.x, hX.y, hZ.x, hZ.y, hy);
+                    } else {
+                        fused_iface<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX, rU,
+                                           eta_lo, eta_hi, hy);
+                    }
+                }
 #pragma unroll
                 for (int f = 0; f < 5; ++f) S.SH[(f * TY + ty) * FX + tx] = hy[f];
                 {
                     float hz[5] = {0, 0, 0, 0, 0};
                     if (do_zeta) {
                         const bool lo = !pk && gk == 0, hi = !pk && gk + 1 == nk - 1;
-                        fused_iface<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
-                                           ring2(kU + 1), lo, hi, hz);
+                        if constexpr (SEP) {
+                            const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
+                            const float hZR = F.h1[2][gidx(kU + 1, nk, pk)].x;
+                            fused_iface_sep<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
+                                                   ring2(kU + 1), lo, hi, hZ.x, hZR, hX.x, hX.y, hY.x, hY.y, hz);
+                        } else {
+                            fused_iface<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
+                                               ring2(kU + 1), lo, hi, hz);
+                        }
                     }
 #pragma unroll
                     for (int f = 0; f < 5; ++f) {
@@ -564,17 +725,24 @@ template <int TY> size_t fused_smem_bytes() { return Geo<TY>::BYTES; }
 
 template <int TY> int fused_prepare()
 {
-    return (int)cudaFuncSetAttribute(k_fused<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    int rc = (int)cudaFuncSetAttribute(k_fused<TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Geo<TY>::BYTES);
+    if (rc) return rc;
+    return (int)cudaFuncSetAttribute(k_fused<TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)Geo<TY>::BYTES);
 }
 
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid, int src,
-                  int dst, int stage, const double *dt, int rhs_only, cudaStream_t st)
+                  int dst, int stage, const double *dt, int rhs_only, int separable, cudaStream_t st)
 {
     dim3 block(FX, TY);
-    k_fused<TY><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                    rhs_only);
+    if (separable)
+        k_fused<TY, true><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
+                                                              rhs_only);
+    else
+        k_fused<TY, false><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
+                                                               rhs_only);
 }
 
 template size_t fused_smem_bytes<16>();
@@ -582,8 +750,8 @@ template size_t fused_smem_bytes<8>();
 template int fused_prepare<16>();
 template int fused_prepare<8>();
 template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                               const double *, int, cudaStream_t);
+                               const double *, int, int, cudaStream_t);
 template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                              const double *, int, cudaStream_t);
+                              const double *, int, int, cudaStream_t);
 
 } // namespace les

@@ -176,6 +176,7 @@ struct FusedParams {
     float k2, k4;           // Turkel-Vatsa constants
     float inv_Re, kap_mol, kap_sgs;
     float suth1, suthS;     // Sutherland: mu = T^1.5 suth1 / (T + suthS)
+    float cs2;              // Smagorinsky C_s^2 (separable form: (C_s Delta)^2 = cs2 (h_x h_y h_z)^(2/3))
 };
 
 // Work-list entry of one jet for the fused stage kernel: items
@@ -185,13 +186,21 @@ struct FusedJet {
     int nbx, nby, nkc;
     int kc;                 // planes per k-chunk
     FusedParams fp;
+    // separable form (Cartesian-product grid): per axis a, for each index,
+    // (h, 1/h, h^(2/3), 0) with h the derivative of coordinate a along axis a
+    const float4 *h1[3];
 };
 
 template <int TY> size_t fused_smem_bytes();
 template <int TY> int fused_prepare();
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
-                  int src, int dst, int stage, const double *dt, int rhs_only, cudaStream_t st);
+                  int src, int dst, int stage, const double *dt, int rhs_only, int separable, cudaStream_t st);
+
+// Separable form: 1-D spacings of a Cartesian-product grid from device
+// coordinates (FP64 derivative stencils of the metric computation).
+void launch_sep_metrics(const double *x, const double *y, const double *z, const int n[3], const int per[3],
+                        const double shift[9], float4 *h1x, float4 *h1y, float4 *h1z, cudaStream_t st);
 
 // Kernel launchers (les_kernels.cu, les_stage.cu), all asynchronous on `st`.
 template <typename real> struct Launch {

@@ -122,6 +122,41 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
     }
 }
 
+// Separable form on a Cartesian-product grid: the spacing h_a(q) = d x_a /
+// d xi^a along each axis, by the same FP64 stencils as the metrics (on such a
+// grid the cofactors are products of these), stored with 1/h_a and h_a^(2/3)
+// in FP32 for the fused stage.
+__global__ void __launch_bounds__(BLOCK) k_sep_metrics(CoordGrid G, float4 *h1x, float4 *h1y, float4 *h1z)
+{
+    const int tot = G.n[0] + G.n[1] + G.n[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        const int a = t < G.n[0] ? 0 : (t < G.n[0] + G.n[1] ? 1 : 2);
+        const int qa = a == 0 ? t : (a == 1 ? t - G.n[0] : t - G.n[0] - G.n[1]);
+        int q[3] = {0, 0, 0};
+        q[a] = qa;
+        const double h = dcoord(G, a, a, q);
+        const double c = cbrt(h);
+        float4 *out = a == 0 ? h1x : (a == 1 ? h1y : h1z);
+        out[qa] = make_float4((float)h, (float)(1.0 / h), (float)(c * c), 0.0f);
+    }
+}
+
+void launch_sep_metrics(const double *x, const double *y, const double *z, const int n[3], const int per[3],
+                        const double shift[9], float4 *h1x, float4 *h1y, float4 *h1z, cudaStream_t st)
+{
+    CoordGrid G;
+    G.X[0] = x;
+    G.X[1] = y;
+    G.X[2] = z;
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = n[a];
+        G.per[a] = per[a];
+    }
+    for (int t = 0; t < 9; ++t) G.shift[t] = shift[t];
+    const int tot = n[0] + n[1] + n[2];
+    k_sep_metrics<<<(tot + BLOCK - 1) / BLOCK, BLOCK, 0, st>>>(G, h1x, h1y, h1z);
+}
+
 // Static per-point fields derived from the metrics (FP64): J = 1/J^-1; per
 // axis a the interface average of J^-1 towards the +a neighbour, its
 // reciprocal, and the norm of metric row a.
