@@ -45,8 +45,8 @@ __constant__ float c_alpha_f[5] = {0.25f, 1.0f / 6.0f, 0.375f, 0.5f, 1.0f};
 //   GD [2][3][NC1] float4  d(u,v,w,T)/d xi_a, a = 0..2
 //   GC [2][2][NC1] float4  (mu_eff, kappa, nu_xi, lb_xi), (nu_eta, lb_eta, nu_zeta, lb_zeta)
 //   MA [2][2][NC1] float4  metric cofactors m0..m3, m4..m7
-//   PB [5][NC2] float2  p T              (point ring)
 //   MB [2][NC1] float2  m8, J^-1
+//   PB [5][NC2] float2  p T              (point ring)
 //   SH [5][TY][FX] float  eta-interface fluxes of the current plane
 //   HX [C2X], HY [C2Y] float4  separable form: (h, 1/h, h^(2/3), 0) of the
 //                              tile's columns / rows, h = dx/dxi resp. dy/deta
@@ -58,9 +58,14 @@ template <int TY> struct Geo {
     static constexpr size_t O_GD = O_PA + 16ull * 5 * NC2;
     static constexpr size_t O_GC = O_GD + 16ull * 2 * 3 * NC1;
     static constexpr size_t O_MA = O_GC + 16ull * 2 * 2 * NC1;
-    static constexpr size_t O_PB = O_MA + 16ull * 2 * 2 * NC1;
-    static constexpr size_t O_MB = O_PB + 8ull * 5 * NC2;
-    static constexpr size_t O_SH = O_MB + 8ull * 2 * NC1;
+    static constexpr size_t O_MB = O_MA + 16ull * 2 * 2 * NC1;
+    static constexpr size_t O_PB = O_MB + 8ull * 2 * NC1;
+    static constexpr size_t O_SH = O_PB + 8ull * 5 * NC2;
+    // separable form: MA/MB hold no metrics; their 20 NT floats stage the
+    // state of the next plane and Q(0) (cp.async), see k_fused
+    static constexpr size_t O_QS = O_MA;                 // float [2 cells][5][NT]
+    static constexpr size_t O_Q0S = O_QS + 4ull * 10 * NT; // float [2 planes][5][NT]
+    static_assert(O_Q0S + 4ull * 10 * NT <= O_PB, "staging fits in MA+MB");
     static constexpr size_t O_HX = O_SH + 4ull * 5 * TY * FX;
     static constexpr size_t O_HY = O_HX + 16ull * C2X;
     static constexpr size_t BYTES = O_HY + 16ull * C2Y;
@@ -71,11 +76,13 @@ template <int TY> struct Sm {
     float2 *PB, *MB;
     float *SH;
     float4 *HX, *HY;
+    float *QS, *Q0S;
     __device__ __forceinline__ explicit Sm(unsigned char *b)
         : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
           GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
           PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH)),
-          HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY))
+          HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY)),
+          QS((float *)(b + Geo<TY>::O_QS)), Q0S((float *)(b + Geo<TY>::O_Q0S))
     {
     }
 };
@@ -93,6 +100,17 @@ __device__ __forceinline__ int gidx(int g, int n, int per)
 // Square root of a strictly positive argument through the hardware
 // reciprocal square root (max. 2 ulp): x * rsqrt(x).
 __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+
+// Asynchronous 4-byte global -> shared copy (completes without the issuing
+// thread waiting; cp_async_wait_all() waits for all of this thread's copies).
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 
 __device__ __forceinline__ float cmp(const float4 &v, int i)
 {
@@ -480,6 +498,33 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             for (int t = 0; t < 2; ++t)
                 if (lc[t] >= 0) rJ2[t] = S.HX[lc[t] % C2X].y * S.HY[lc[t] / C2X].y;
         }
+        // separable form: the state of plane kq (this thread's load cells) and
+        // Q(0) of its output column at plane ku are staged in shared memory
+        // one iteration ahead by asynchronous copies, so the load phase and the
+        // update find them there; each thread reads only what it copied
+        auto stage_q = [&](int kq) {
+            const int gk = gidx(kq, nk, pk);
+            if (kq > k1 + 2 || gk < 0) return;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (lc[t] < 0) continue;
+                const long long o = gk * plane + lo2[t];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) cp_async4(&S.QS[(t * 5 + f) * G_::NT + tid], Qs + f * fs + o);
+            }
+        };
+        auto stage_q0 = [&](int ku) {
+            const int gk = gidx(ku, nk, pk);
+            if (rhs_only || !out_col || ku < k0 || ku >= k1 || gk < 0) return;
+            const long long o = gk * plane + ocol;
+            const float *Q0g = J.q[0];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) cp_async4(&S.Q0S[(ring2(ku) * 5 + f) * G_::NT + tid], Q0g + f * fs + o);
+        };
+        if constexpr (SEP) {
+            stage_q(k0 - 3);
+            cp_async_commit();
+        }
         for (int kL = k0 - 3; kL <= k1 + 2; ++kL) {
 #pragma unroll
             for (int t = 0; t < 5; ++t) sl[t] = sl[t + 1];
@@ -508,6 +553,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             }
             {
                 const int gk = gidx(kL, nk, pk);
+                if constexpr (SEP) cp_async_wait_all();
                 if (gk >= 0) {
                     const int sb = sl[5] * N2;
                     const float rhzL = SEP ? F.h1[2][gk].y : 0.0f;
@@ -515,12 +561,20 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     for (int t = 0; t < 2; ++t) {
                         if (lc[t] < 0) continue;
                         const long long o = gk * plane + lo2[t];
+                        float qv[5];
+                        if constexpr (SEP) {
+#pragma unroll
+                            for (int f = 0; f < 5; ++f) qv[f] = S.QS[(t * 5 + f) * G_::NT + tid];
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < 5; ++f) qv[f] = Qs[f * fs + o];
+                        }
                         const float rj = SEP ? rJ2[t] * rhzL : M[MET_J * fs + o];
-                        const float rho = Qs[o] * rj;
+                        const float rho = qv[0] * rj;
                         const float rr = 1.0f / rho;
                         const float rrj = rj * rr;
-                        const float u = Qs[fs + o] * rrj, v = Qs[2 * fs + o] * rrj, w = Qs[3 * fs + o] * rrj;
-                        const float e = Qs[4 * fs + o] * rj;
+                        const float u = qv[1] * rrj, v = qv[2] * rrj, w = qv[3] * rrj;
+                        const float e = qv[4] * rj;
                         const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
                         S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
                         S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
@@ -611,6 +665,13 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 S.GC[(rG * 2 + 1) * N1 + c1] = make_float4(dd[1].nu, lam[1] + s01 + s12, dd[2].nu, lam[2] + s02 + s12);
             }
             __syncthreads();
+            if constexpr (SEP) {
+                // next plane's state and the next update's Q(0), in flight
+                // during the interface arithmetic
+                stage_q(kL + 1);
+                stage_q0(kL - 2);
+                cp_async_commit();
+            }
             // ---- interfaces and update of plane kU = kL - 3 ----
             const int kU = kL - 3;
             if (kU >= k0 - 1) {
@@ -696,7 +757,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
                 // Q(0) of the updated point, requested before the exchange barrier
                 float q0v[5] = {0, 0, 0, 0, 0};
-                if (upd && !rhs_only) {
+                if (!SEP && upd && !rhs_only) {
                     const float *Q0 = J.q[0];
 #pragma unroll
                     for (int f = 0; f < 5; ++f) q0v[f] = Q0[f * fs + o];
@@ -709,6 +770,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                         for (int f = 0; f < 5; ++f) J.rhs[f * fs + o] = R[f];
                     } else {
+                        if constexpr (SEP) {
+#pragma unroll
+                            for (int f = 0; f < 5; ++f) q0v[f] = S.Q0S[(ring2(kU) * 5 + f) * G_::NT + tid];
+                        }
                         const float adt = c_alpha_f[stage] * (float)dt[jet];
                         float *Qd = J.q[dst];
 #pragma unroll
