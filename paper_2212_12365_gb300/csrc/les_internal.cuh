@@ -20,7 +20,8 @@ constexpr int NF = 5;         // conserved variables
 // to the +a neighbour, its reciprocal, and |row a| = sqrt(sum_c m_ac^2).
 constexpr int NMET = 21;      // fields of every precision
 constexpr int MET_A0 = 21;    // FP64 only: 27 interface tables, see below
-constexpr int NMET64 = 48;
+constexpr int MET_K0 = 48;    // FP64 only: 9 interface contractions, see below
+constexpr int NMET64 = 57;
 constexpr int MET_JINV = 9;
 constexpr int MET_CSD2 = 10;
 constexpr int MET_J = 11;
@@ -32,6 +33,9 @@ constexpr int MET_NORM = 18;  // + a
 // interface J^-1, times 1/2 for b != a: the chain-rule weights of the compact
 // viscous flux applied to the normal difference (b == a) and to the SUM of
 // the two points' central differences (b != a).
+// FP64 only, per axis a at [MET_K0 + 3a + b]: K_b = sum_c A_ac A_bc (same
+// tables), so that the flux-direction contraction of a gradient,
+// sum_c A_ac d phi/d x_c, is sum_b K_b D_b.
 // Per-point stage fields: primitives, Sutherland viscosity, lambda-bar,
 // the unscaled conserved vector W0..W3 (= rho is P_RHO) and rho H = e + p,
 // and the inviscid point fluxes F_a (5 each) at P_F0 + 5a + f.

@@ -189,11 +189,16 @@ __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long 
             met[(MET_NORM + a) * fs + o] = sqrt(mx * mx + my * my + mz * mz);
             if (iface_tables) {
                 const double rjb = 1.0 / jb;
+                double A[9];
                 for (int b = 0; b < 3; ++b)
                     for (int c = 0; c < 3; ++c) {
                         const double mc = 0.5 * (met[(3 * b + c) * fs + o] + met[(3 * b + c) * fs + oR]);
-                        met[(MET_A0 + 9 * a + 3 * b + c) * fs + o] = mc * rjb * (b == a ? 1.0 : 0.5);
+                        A[3 * b + c] = mc * rjb * (b == a ? 1.0 : 0.5);
+                        met[(MET_A0 + 9 * a + 3 * b + c) * fs + o] = A[3 * b + c];
                     }
+                for (int b = 0; b < 3; ++b)
+                    met[(MET_K0 + 3 * a + b) * fs + o] =
+                        A[3 * a] * A[3 * b] + A[3 * a + 1] * A[3 * b + 1] + A[3 * a + 2] * A[3 * b + 2];
             }
         }
     }

@@ -167,24 +167,26 @@ __global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict_
 #pragma unroll
         for (int t = 0; t < 9; ++t) m[t] = M[t * fs + lp];
         const real rj = M[MET_J * fs + lp];
-        real gu[3][3]; // d u_i / d x_c (chain rule through the metric cofactors)
+        // d u_i / d x_c = J g_ic with g_ic = sum_b m_bc d u_i / d xi^b (chain
+        // rule through the metric cofactors); 2 S_ij S_ij = J^2 (2 sum_i g_ii^2
+        // + sum_{i<c} (g_ic + g_ci)^2)
+        real g[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                gu[i][c] = (m[c] * d[i][0] + m[3 + c] * d[i][1] + m[6 + c] * d[i][2]) * rj;
-        real ss = real(0);
+            for (int c = 0; c < 3; ++c) g[i][c] = m[c] * d[i][0] + m[3 + c] * d[i][1] + m[6 + c] * d[i][2];
+        real sd = real(0), so = real(0);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            ss += gu[i][i] * gu[i][i];
+            sd += g[i][i] * g[i][i];
 #pragma unroll
             for (int c = i + 1; c < 3; ++c) {
-                const real sic = real(0.5) * (gu[i][c] + gu[c][i]);
-                ss += real(2) * sic * sic;
+                const real t = g[i][c] + g[c][i];
+                so += t * t;
             }
         }
         // Smagorinsky: mu_sgs = rho (Cs Delta)^2 (2 S_ij S_ij)^1/2
-        const real mus = P[P_RHO * fs + lp] * M[MET_CSD2 * fs + lp] * sqrt(real(2) * ss);
+        const real mus = P[P_RHO * fs + lp] * M[MET_CSD2 * fs + lp] * rj * sqrt(real(2) * sd + so);
         const real mu = P[P_MU * fs + lp];
         G[G_MUSGS * fs + lp] = mus;
         G[G_MUEFF * fs + lp] = mu * (real)J.inv_Re + mus;
@@ -258,40 +260,43 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
         for (int b = 0; b < 3; ++b)
             D[f][b] = (b == a) ? P[pf[f] * fs + R] - P[pf[f] * fs + L]
                                : G[(3 * f + b) * fs + L] + G[(3 * f + b) * fs + R];
-    real Ab[9];
+    real Ab[9], K[3];
 #pragma unroll
     for (int t = 0; t < 9; ++t) Ab[t] = A[t * fs];
-    real gu[4][3];
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+    for (int t = 0; t < 3; ++t) K[t] = M[(MET_K0 + 3 * a + t) * fs + L];
+    const real *mr = Ab + 3 * a; // averaged cofactor row a / interface J^-1
+    // The flux needs only the row-a contraction of the stress tensor,
+    //   s_i = sum_c mr_c tau_ci = coef (1/2 (X_i + Y_i) - mr_i tr/3),
+    // with X_i = sum_c mr_c du_i/dx_c = sum_b K_b D_ib,
+    //      Y_i = sum_c mr_c du_c/dx_i = sum_b Ab_bi (sum_c mr_c D_cb),
+    //      tr  = div u = sum_i sum_b Ab_bi D_ib,
+    // and the energy flux sum_c mr_c (tau_cj u_j + kappa dT/dx_c) =
+    // s . u_interface + kappa X_T; tau itself is never formed.
+    real X[4];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gu[f][c] = Ab[c] * D[f][0] + Ab[3 + c] * D[f][1] + Ab[6 + c] * D[f][2];
-    const real div3 = (gu[0][0] + gu[1][1] + gu[2][2]) * real(1.0 / 3.0);
+    for (int f = 0; f < 4; ++f) X[f] = K[0] * D[f][0] + K[1] * D[f][1] + K[2] * D[f][2];
+    real w[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) w[b] = mr[0] * D[0][b] + mr[1] * D[1][b] + mr[2] * D[2][b];
+    real tr = real(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tr += Ab[i] * D[i][0] + Ab[3 + i] * D[i][1] + Ab[6 + i] * D[i][2];
     const real coef = (G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]) * jb; // 2 x average x J^-1
     const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]) * jb;
-    real tau[3][3];
+    const real ch = real(0.5) * coef, ct = coef * tr * real(1.0 / 3.0);
+    real sv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        tau[i][i] = coef * (gu[i][i] - div3);
-#pragma unroll
-        for (int c = i + 1; c < 3; ++c) {
-            tau[i][c] = coef * real(0.5) * (gu[i][c] + gu[c][i]);
-            tau[c][i] = tau[i][c];
-        }
+        const real Y = Ab[i] * w[0] + Ab[3 + i] * w[1] + Ab[6 + i] * w[2];
+        sv[i] = ch * (X[i] + Y) - ct * mr[i];
+        H[1 + i] -= sv[i];
     }
-    const real vb[3] = {real(0.5) * (P[P_U * fs + L] + P[P_U * fs + R]),
-                        real(0.5) * (P[P_V * fs + L] + P[P_V * fs + R]),
-                        real(0.5) * (P[P_W * fs + L] + P[P_W * fs + R])};
-    const real *mr = Ab + 3 * a;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) H[1 + i] -= mr[0] * tau[0][i] + mr[1] * tau[1][i] + mr[2] * tau[2][i];
-    real fe = real(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // beta_c = tau_cj u_j - q_c with q = -k grad T
-        const real beta = tau[c][0] * vb[0] + tau[c][1] * vb[1] + tau[c][2] * vb[2] + kap * gu[3][c];
-        fe += mr[c] * beta;
-    }
+    // beta = tau u - q, q = -kappa grad T; interface velocity = average
+    const real fe = real(0.5) * ((P[P_U * fs + L] + P[P_U * fs + R]) * sv[0] +
+                                 (P[P_V * fs + L] + P[P_V * fs + R]) * sv[1] +
+                                 (P[P_W * fs + L] + P[P_W * fs + R]) * sv[2]) +
+                    kap * X[3];
     H[4] -= fe;
 }
 
