@@ -207,11 +207,11 @@ __device__ __forceinline__ void fused_iface(const Sm<TY> &S, const FusedParams &
         const float se2 = sc * eps2, se4 = sc * eps4;
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
+            // dW(+3/2) - 2 dW(+1/2) + dW(-1/2) = W(R+1) - W(L-1) - 3 dW(+1/2); at a
+            // non-periodic end the mirrored difference makes W(R+1) = W(L), W(L-1) = W(R)
             const float dW0 = WR[f] - LW[f];
-            const float dWp = hi_end ? -dW0 : WRp[f] - WR[f];
-            const float dWm = lo_end ? -dW0 : LW[f] - WLm[f];
-            const float d3 = dWp - 2.0f * dW0 + dWm;
-            H[f] -= se2 * dW0 - se4 * d3;
+            const float d3 = ((hi_end ? LW[f] : WRp[f]) - (lo_end ? WR[f] : WLm[f])) - 3.0f * dW0;
+            H[f] += se4 * d3 - se2 * dW0;
         }
     }
     // compact viscous + SGS flux
@@ -325,11 +325,11 @@ __device__ __forceinline__ void fused_iface_sep(const Sm<TY> &S, const FusedPara
         const float se2 = sc * eps2, se4 = sc * eps4;
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
+            // dW(+3/2) - 2 dW(+1/2) + dW(-1/2) = W(R+1) - W(L-1) - 3 dW(+1/2); at a
+            // non-periodic end the mirrored difference makes W(R+1) = W(L), W(L-1) = W(R)
             const float dW0 = WR[f] - LW[f];
-            const float dWp = hi_end ? -dW0 : WRp[f] - WR[f];
-            const float dWm = lo_end ? -dW0 : LW[f] - WLm[f];
-            const float d3 = dWp - 2.0f * dW0 + dWm;
-            H[f] -= se2 * dW0 - se4 * d3;
+            const float d3 = ((hi_end ? LW[f] : WRp[f]) - (lo_end ? WR[f] : WLm[f])) - 3.0f * dW0;
+            H[f] += se4 * d3 - se2 * dW0;
         }
     }
     // compact viscous + SGS flux: only row A of the stress tensor is needed

@@ -238,11 +238,14 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
         const real *W = P + wf[f] * fs;
         const real wL = W[L], wR = W[R];
         const real dW0 = wR - wL;
-        const real dWp = hi_end ? -dW0 : W[Rp] - wR;
-        const real dWm = lo_end ? -dW0 : wL - W[Lm];
-        const real d3 = dWp - real(2) * dW0 + dWm;
+        // third difference dW(+3/2) - 2 dW(+1/2) + dW(-1/2) = W(R+1) - W(L-1) - 3 dW(+1/2);
+        // the mirrored difference at a non-periodic end, dW(outside) = -dW(+1/2),
+        // is the missing point W(R+1) = W(L) (resp. W(L-1) = W(R))
+        const real wRp = hi_end ? wL : W[Rp];
+        const real wLm = lo_end ? wR : W[Lm];
+        const real d3 = (wRp - wLm) - real(3) * dW0;
         const real *F = P + (P_F0 + 5 * a + f) * fs;
-        H[f] = real(0.5) * (F[L] + F[R]) - (se2 * dW0 - se4 * d3);
+        H[f] = real(0.5) * (F[L] + F[R]) + (se4 * d3 - se2 * dW0);
     }
     // compact viscous + SGS flux: normal derivative from the two points,
     // tangential derivatives averaged, coefficients/metrics/velocity averaged.
