@@ -33,6 +33,7 @@ struct JetHost {
     char *met, *q[3], *prim, *grad, *hflux, *rhs;
     double *jinv64, *inflow_r;
     float4 *h1[3];                     // FP32: 1-D spacings of a product grid (separable form)
+    float4 *mp;                        // FP32 general form: packed static fields (4 float4 / point)
     int nblk_pt, nblk_bc[3];
 };
 
@@ -167,6 +168,8 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     size_t o_rhs = take(NF * fb);
     size_t o_inr = take((size_t)g->nj * g->nk * 8);
     size_t o_h1 = prec == LES_FP32 ? take((size_t)(g->ni + g->nj + g->nk) * 16) : 0;
+    const bool packed = g->precision == LES_FP32; // general FP32 form only
+    size_t o_mp = packed ? take((size_t)J.npad * 64) : 0;
     J.bytes = off;
     // store offsets relative to the jet region in the pointers for now
     J.met = (char *)o_met;
@@ -182,6 +185,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     J.h1[0] = prec == LES_FP32 ? (float4 *)o_h1 : nullptr;
     J.h1[1] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)g->ni * 16) : nullptr;
     J.h1[2] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)(g->ni + g->nj) * 16) : nullptr;
+    J.mp = packed ? (float4 *)o_mp : nullptr;
 }
 
 // Storage precision of a descriptor's precision code.
@@ -264,6 +268,9 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.inv_Re = 1.0 / p.Re;
     D.kap_mol = 1.0 / (p.Re * p.Pr * (p.gamma - 1.0));
     D.kap_sgs = 1.0 / (p.Pr_sgs * (p.gamma - 1.0));
+    D.bc_g1 = 1.0 / (p.gamma - 1.0);
+    D.bc_rg = 1.0 / p.gamma;
+    D.bc_cinf = std::sqrt(p.gamma * (1.0 / p.gamma) / p.TR);
     D.seed = (unsigned long long)p.seed;
     (void)h;
 }
@@ -296,6 +303,10 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(J.jinv64, met64 + MET_JINV * J.fs, (size_t)J.fs * 8,
                            cudaMemcpyDeviceToDevice, h->st));
+        if (J.mp) {
+            launch_pack_metrics((const float *)J.met, J.fs, J.mp, J.npad, h->st);
+            CK(cudaGetLastError());
+        }
     }
     // radius of the inflow-face points
     std::vector<double> r((size_t)J.n[1] * J.n[2]);
@@ -469,6 +480,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
         J.inflow_r = (double *)(jb + (size_t)J.inflow_r);
         for (int a = 0; a < 3; ++a)
             if (J.h1[a]) J.h1[a] = (float4 *)(jb + (size_t)J.h1[a]);
+        if (J.mp) J.mp = (float4 *)(jb + (size_t)J.mp);
     }
     for (int j = 0; j < njets; ++j) {
         int rc = setup_jet<real>(h, h->J[j], &g[j]);
@@ -498,6 +510,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             F.suthS = (float)S;
             F.cs2 = (float)(pp.Cs * pp.Cs);
             for (int a = 0; a < 3; ++a) h->fj[j].h1[a] = h->J[j].h1[a];
+            h->fj[j].mp = h->J[j].mp;
         }
         int rc = set_fused_tiling(h, 8, 32);
         if (rc) return bail(rc);

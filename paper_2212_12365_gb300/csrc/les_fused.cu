@@ -440,6 +440,8 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         const long long plane = (long long)nj * J.pitch;
         const float *__restrict__ Qs = J.q[src];
         const float *__restrict__ M = J.met;
+        float *__restrict__ Qd = J.q[dst];
+        const float adt = rhs_only ? 0.0f : c_alpha_f[stage] * (float)dt[jet];
 
         // this thread's column (R1 cell)
         const int gi = gidx(ib + tx, ni, pi), gj = gidx(jb + ty, nj, pj);
@@ -534,51 +536,70 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             const bool g_act = kG >= k0 - 1 && gkG >= 0 && col_ok;
             const int rG = ring2(kG);
             // ---- static fields of plane kG (R1, this thread's column) and
-            //      load + primitives of plane kL on R2 ----
-            float m[9], csd2 = 0.0f, rjG = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
+            //      load + primitives of plane kL on R2; every global load of
+            //      the phase is issued before the first shared-memory store,
+            //      so that their latencies overlap ----
+            float m[9], jinvG = 0.0f, csd2 = 0.0f, rjG = 0.0f, nrm[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int t = 0; t < 9; ++t) m[t] = 0.0f;
             if (!SEP && g_act) {
-                const long long o = gkG * plane + ocol;
+                const float4 *mp = F.mp + 4 * (gkG * plane + ocol);
+                const float4 a0 = mp[0], a1 = mp[1], a2 = mp[2], a3 = mp[3];
+                m[0] = a0.x; m[1] = a0.y; m[2] = a0.z; m[3] = a0.w;
+                m[4] = a1.x; m[5] = a1.y; m[6] = a1.z; m[7] = a1.w;
+                m[8] = a2.x;
+                jinvG = a2.y;
+                csd2 = a2.z;
+                rjG = a2.w;
+                nrm[0] = a3.x;
+                nrm[1] = a3.y;
+                nrm[2] = a3.z;
+            }
+            const int gkL = gidx(kL, nk, pk);
+            float qv[2][5], rjc[2];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) m[t] = M[t * fs + o];
-                const float jinv = M[MET_JINV * fs + o];
-                csd2 = M[MET_CSD2 * fs + o];
-                rjG = M[MET_J * fs + o];
+            for (int t = 0; t < 2; ++t) {
+                rjc[t] = 0.0f;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) nrm[a] = M[(MET_NORM + a) * fs + o];
+                for (int f = 0; f < 5; ++f) qv[t][f] = 0.0f;
+            }
+            if constexpr (SEP) cp_async_wait_all();
+            if (gkL >= 0) {
+                const float rhzL = SEP ? F.h1[2][gkL].y : 0.0f;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (lc[t] < 0) continue;
+                    const long long o = gkL * plane + lo2[t];
+                    if constexpr (SEP) {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
+                        rjc[t] = rJ2[t] * rhzL;
+                    } else {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
+                        rjc[t] = M[MET_J * fs + o];
+                    }
+                }
+            }
+            if (!SEP && g_act) {
                 S.MA[(rG * 2 + 0) * N1 + c1] = make_float4(m[0], m[1], m[2], m[3]);
                 S.MA[(rG * 2 + 1) * N1 + c1] = make_float4(m[4], m[5], m[6], m[7]);
-                S.MB[rG * N1 + c1] = make_float2(m[8], jinv);
+                S.MB[rG * N1 + c1] = make_float2(m[8], jinvG);
             }
-            {
-                const int gk = gidx(kL, nk, pk);
-                if constexpr (SEP) cp_async_wait_all();
-                if (gk >= 0) {
-                    const int sb = sl[5] * N2;
-                    const float rhzL = SEP ? F.h1[2][gk].y : 0.0f;
+            if (gkL >= 0) {
+                const int sb = sl[5] * N2;
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        if (lc[t] < 0) continue;
-                        const long long o = gk * plane + lo2[t];
-                        float qv[5];
-                        if constexpr (SEP) {
-#pragma unroll
-                            for (int f = 0; f < 5; ++f) qv[f] = S.QS[(t * 5 + f) * G_::NT + tid];
-                        } else {
-#pragma unroll
-                            for (int f = 0; f < 5; ++f) qv[f] = Qs[f * fs + o];
-                        }
-                        const float rj = SEP ? rJ2[t] * rhzL : M[MET_J * fs + o];
-                        const float rho = qv[0] * rj;
-                        const float rr = 1.0f / rho;
-                        const float rrj = rj * rr;
-                        const float u = qv[1] * rrj, v = qv[2] * rrj, w = qv[3] * rrj;
-                        const float e = qv[4] * rj;
-                        const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
-                        S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
-                        S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
-                    }
+                for (int t = 0; t < 2; ++t) {
+                    if (lc[t] < 0) continue;
+                    const float rj = rjc[t];
+                    const float rho = qv[t][0] * rj;
+                    const float rr = 1.0f / rho;
+                    const float rrj = rj * rr;
+                    const float u = qv[t][1] * rrj, v = qv[t][2] * rrj, w = qv[t][3] * rrj;
+                    const float e = qv[t][4] * rj;
+                    const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
+                    S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
+                    S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
                 }
             }
             __syncthreads();
@@ -669,7 +690,6 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 // next plane's state and the next update's Q(0), in flight
                 // during the interface arithmetic
                 stage_q(kL + 1);
-                stage_q0(kL - 2);
                 cp_async_commit();
             }
             // ---- interfaces and update of plane kU = kL - 3 ----
@@ -683,6 +703,13 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 const bool do_zeta = plane_ok && out_col && (pk || gk < nk - 1);
                 const bool upd = !first && plane_ok && out_col && kU < k1;
                 const long long o = (long long)(plane_ok ? gk : 0) * plane + ocol;
+                // separable form: Q(0) of the updated point, in flight during the interfaces
+                float q0s[5] = {0, 0, 0, 0, 0};
+                if (SEP && upd && !rhs_only) {
+                    const float *Q0 = J.q[0];
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) q0s[f] = Q0[f * fs + o];
+                }
                 const int rU = ring2(kU), sU = sl[2] * N2;
                 OwnPt L;
                 if (do_xi || do_eta || do_zeta) {
@@ -772,10 +799,8 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     } else {
                         if constexpr (SEP) {
 #pragma unroll
-                            for (int f = 0; f < 5; ++f) q0v[f] = S.Q0S[(ring2(kU) * 5 + f) * G_::NT + tid];
+                            for (int f = 0; f < 5; ++f) q0v[f] = q0s[f];
                         }
-                        const float adt = c_alpha_f[stage] * (float)dt[jet];
-                        float *Qd = J.q[dst];
 #pragma unroll
                         for (int f = 0; f < 5; ++f) Qd[f * fs + o] = q0v[f] - adt * R[f];
                     }

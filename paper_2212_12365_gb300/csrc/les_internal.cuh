@@ -81,6 +81,7 @@ struct JetDev {
     double inv_Re;     // 1/Re (0 for an inviscid run)
     double kap_mol;    // mu -> conductivity: 1/(Re Pr (gamma-1))
     double kap_sgs;    // mu_sgs -> conductivity: 1/(Pr_sgs (gamma-1))
+    double bc_g1, bc_rg, bc_cinf; // 1/(gamma-1), 1/gamma, ambient sound speed (1/TR)^1/2
     unsigned long long seed;
     long long npts_pad; // nk*nj*pitch
 };
@@ -193,6 +194,9 @@ struct FusedJet {
     // separable form (Cartesian-product grid): per axis a, for each index,
     // (h, 1/h, h^(2/3), 0) with h the derivative of coordinate a along axis a
     const float4 *h1[3];
+    // general form: the static fields of each point packed as four float4
+    // records (m0..m3 | m4..m7 | m8, J^-1, (Cs Delta)^2, J | row norms, 0)
+    const float4 *mp;
 };
 
 template <int TY> size_t fused_smem_bytes();
@@ -203,6 +207,7 @@ void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int 
 
 // Separable form: 1-D spacings of a Cartesian-product grid from device
 // coordinates (FP64 derivative stencils of the metric computation).
+void launch_pack_metrics(const float *met, long long fs, float4 *mp, long long npad, cudaStream_t st);
 void launch_sep_metrics(const double *x, const double *y, const double *z, const int n[3], const int per[3],
                         const double shift[9], float4 *h1x, float4 *h1y, float4 *h1z, cudaStream_t st);
 

@@ -9,6 +9,7 @@
 // spans one or many jets (batched form); the per-point arithmetic does not
 // depend on the map, so a jet gives the same bits alone or in a batch.
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
 
 #include "les_internal.cuh"
@@ -120,6 +121,28 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
         double delta = cbrt(jinv); // filter width: cube root of the cell volume
         met[MET_CSD2 * fs + o] = (Cs * delta) * (Cs * delta);
     }
+}
+
+// General FP32 form: the 15 static fields the fused stage reads per point,
+// packed into four consecutive float4 records so that the load phase fetches
+// them with four vector loads from one array instead of fifteen.
+__global__ void __launch_bounds__(BLOCK) k_pack_metrics(const float *met, long long fs, float4 *mp,
+                                                        long long npad)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npad;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float *m = met + p;
+        mp[4 * p + 0] = make_float4(m[0], m[fs], m[2 * fs], m[3 * fs]);
+        mp[4 * p + 1] = make_float4(m[4 * fs], m[5 * fs], m[6 * fs], m[7 * fs]);
+        mp[4 * p + 2] = make_float4(m[8 * fs], m[MET_JINV * fs], m[MET_CSD2 * fs], m[MET_J * fs]);
+        mp[4 * p + 3] = make_float4(m[MET_NORM * fs], m[(MET_NORM + 1) * fs], m[(MET_NORM + 2) * fs], 0.0f);
+    }
+}
+
+void launch_pack_metrics(const float *met, long long fs, float4 *mp, long long npad, cudaStream_t st)
+{
+    k_pack_metrics<<<(int)std::min<long long>((npad + BLOCK - 1) / BLOCK, 65535LL * 4), BLOCK, 0, st>>>(met, fs, mp,
+                                                                                                      npad);
 }
 
 // Separable form on a Cartesian-product grid: the spacing h_a(q) = d x_a /
@@ -244,20 +267,29 @@ template <typename T> struct PrimT {
     T rho, u[3], p;
 };
 
-template <typename T> __device__ __forceinline__ void cons_t(const PrimT<T> &s, T g, T Q[5])
+// Per-jet constants of the boundary arithmetic: 1/(gamma-1), 1/gamma and the
+// ambient speed of sound; reciprocals replace the divisions of the formulas
+// (FP64 division is a long instruction sequence on this GPU).
+template <typename T> struct BcK {
+    T g, g1, rg, TR, cinf;
+};
+
+template <typename T> __device__ __forceinline__ void cons_t(const PrimT<T> &s, const BcK<T> &k, T Q[5])
 {
     Q[0] = s.rho;
     Q[1] = s.rho * s.u[0];
     Q[2] = s.rho * s.u[1];
     Q[3] = s.rho * s.u[2];
-    Q[4] = s.p / (g - T(1)) + T(0.5) * s.rho * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+    Q[4] = s.p * k.g1 + T(0.5) * s.rho * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
 }
 
-template <typename T> __device__ __forceinline__ PrimT<T> prim_t(const T Q[5], T g)
+// Primitives of a conserved vector; rr = 1/rho.
+template <typename T> __device__ __forceinline__ PrimT<T> prim_t(const T Q[5], T g, T &rr)
 {
     PrimT<T> s;
     s.rho = Q[0];
-    for (int c = 0; c < 3; ++c) s.u[c] = Q[1 + c] / Q[0];
+    rr = T(1) / Q[0];
+    for (int c = 0; c < 3; ++c) s.u[c] = Q[1 + c] * rr;
     s.p = (g - T(1)) * (Q[4] - T(0.5) * Q[0] * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]));
     return s;
 }
@@ -274,17 +306,20 @@ template <typename P> __device__ __forceinline__ double bc_pow(double x, double 
 // Far field (Sec. "Far Field Boundary"): Riemann invariants along the unit
 // outward normal n; R- from the ambient at rest, R+ from the interior point.
 template <typename T, typename P = T>
-__device__ void bc_farfield(T g, T TR, const T Qe[5], const T n[3], T Qf[5])
+__device__ void bc_farfield(const BcK<T> &k, const T Qe[5], const T n[3], T Qf[5])
 {
-    const PrimT<T> e = prim_t(Qe, g);
-    const T pinf = T(1) / g, rinf = TR;
-    const T ce = sqrt(g * e.p / e.rho), cinf = sqrt(g * pinf / rinf);
+    const T g = k.g;
+    T rr;
+    const PrimT<T> e = prim_t(Qe, g, rr);
+    const T pinf = k.rg, rinf = k.TR;
+    const T ce2 = g * e.p * rr; // c_e^2
+    const T rce = rsqrt(ce2), ce = ce2 * rce;
     const T qne = e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2];
-    const T rp = qne + T(2) * ce / (g - T(1));
-    const T rm = T(0) - T(2) * cinf / (g - T(1));
+    const T rp = qne + T(2) * ce * k.g1;
+    const T rm = T(0) - T(2) * k.cinf * k.g1;
     const T qnf = T(0.5) * (rp + rm);
     const T cf = T(0.25) * (g - T(1)) * (rp - rm);
-    const T mn = qne / ce;
+    const T mn = qne * rce;
     PrimT<T> f;
     if (mn >= T(1)) {
         for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
@@ -294,31 +329,34 @@ __device__ void bc_farfield(T g, T TR, const T Qe[5], const T n[3], T Qf[5])
         f.rho = rinf;
         f.u[0] = f.u[1] = f.u[2] = T(0);
         f.p = pinf;
-        cons_t(f, g, Qf);
+        cons_t(f, k, Qf);
         return;
     }
     if (mn >= T(0)) { // subsonic outflow: entropy and tangential velocity from inside
+        // rho_f = (rho_e^gamma c_f^2 / (gamma p_e))^(1/(gamma-1)), gamma p_e = rho_e c_e^2
         for (int c = 0; c < 3; ++c) f.u[c] = e.u[c] + (qnf - qne) * n[c];
-        f.rho = bc_pow<P>(bc_pow<P>(e.rho, g) * cf * cf / (g * e.p), T(1) / (g - T(1)));
-    } else { // subsonic inflow: from the ambient (q_n,inf = 0)
+        f.rho = bc_pow<P>(bc_pow<P>(e.rho, g) * cf * cf * (rr * rce * rce), k.g1);
+    } else { // subsonic inflow: from the ambient (q_n,inf = 0, gamma p_inf = 1)
         for (int c = 0; c < 3; ++c) f.u[c] = T(0) + (qnf - T(0)) * n[c];
-        f.rho = bc_pow<P>(bc_pow<P>(rinf, g) * cf * cf / (g * pinf), T(1) / (g - T(1)));
+        f.rho = bc_pow<P>(bc_pow<P>(rinf, g) * cf * cf, k.g1);
     }
-    f.p = f.rho * cf * cf / g;
-    cons_t(f, g, Qf);
+    f.p = f.rho * cf * cf * k.rg;
+    cons_t(f, k, Qf);
 }
 
 // Exit (Sec. "Exit Boundary Condition").
-template <typename T> __device__ void bc_exit(T g, const T Qe[5], const T n[3], T Qf[5])
+template <typename T> __device__ void bc_exit(const BcK<T> &k, const T Qe[5], const T n[3], T Qf[5])
 {
-    const PrimT<T> e = prim_t(Qe, g);
-    const T ce = sqrt(g * e.p / e.rho);
-    if ((e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2]) / ce >= T(1)) {
+    const T g = k.g;
+    T rr;
+    const PrimT<T> e = prim_t(Qe, g, rr);
+    if ((e.u[0] * n[0] + e.u[1] * n[1] + e.u[2] * n[2]) * rsqrt(g * e.p * rr) >= T(1)) {
         for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
         return;
     }
-    const T ei = e.p / ((g - T(1)) * e.rho);
-    const T rho = (T(1) / g) / ((g - T(1)) * ei);
+    // p_f = p_inf = 1/gamma with the interior internal energy e_i = p/((gamma-1) rho)
+    const T ei = e.p * k.g1 * rr;
+    const T rho = e.rho / (g * e.p);
     Qf[0] = rho;
     Qf[1] = rho * e.u[0];
     Qf[2] = rho * e.u[1];
@@ -363,7 +401,8 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         const long long fs = J.fs;
         real *Qd = J.q[dst];
         using T = double; // boundary arithmetic in FP64 (transcendental pow in the state precision)
-        const T g = (T)J.gamma;
+        const BcK<T> k{(T)J.gamma, (T)J.bc_g1, (T)J.bc_rg, (T)J.TR, (T)J.bc_cinf};
+        const T g = k.g;
         // unit outward normal from the face point's metric row
         T n[3], nn = T(0);
         const T sg = side ? T(1) : T(-1);
@@ -371,21 +410,22 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
             n[c] = sg * J.met[(3 * axis + c) * fs + F];
             nn += n[c] * n[c];
         }
-        nn = sqrt(nn);
-        for (int c = 0; c < 3; ++c) n[c] /= nn;
+        const T rn = rsqrt(nn);
+        for (int c = 0; c < 3; ++c) n[c] *= rn;
         const T jinvE = (T)J.jinv64[E], jinvF = (T)J.jinv64[F];
+        const T rjE = T(1) / jinvE;
         T Qe[5], Qf[5];
-        for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] / jinvE;
+        for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] * rjE;
         if (type == LES_BC_FARFIELD) {
-            bc_farfield<T, real>(g, (T)J.TR, Qe, n, Qf);
+            bc_farfield<T, real>(k, Qe, n, Qf);
         } else if (type == LES_BC_EXIT) {
-            bc_exit<T>(g, Qe, n, Qf);
+            bc_exit<T>(k, Qe, n, Qf);
         } else if (type == LES_BC_INFLOW_JET) {
             const int jj = qf[1], kk = qf[2];
             const T rr = (T)J.inflow_r[(long long)kk * J.n[1] + jj];
             const T ut = T(0.5) * (T(1) + tanh((T(0.5) - rr) / (T(2) * (T)J.theta)));
             if (ut < T(0.01)) {
-                bc_farfield<T, real>(g, (T)J.TR, Qe, n, Qf);
+                bc_farfield<T, real>(k, Qe, n, Qf);
             } else {
                 const T M = (T)J.mach;
                 const T Tt = (T(1) / (T)J.TR) * (T(1) - ut) + ut + T(0.5) * (g - T(1)) * M * M * ut * (T(1) - ut);
@@ -404,7 +444,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
                         s.u[c] += (T)(J.noise_amp * J.mach * (2.0 * h - 1.0));
                     }
                 }
-                cons_t(s, g, Qf);
+                cons_t(s, k, Qf);
             }
         } else {
             continue;
