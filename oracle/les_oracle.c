@@ -53,6 +53,17 @@
  *       Dirichlet where the profile is >= 0.01, far field elsewhere.
  *   R16 time level 0 carries no inflow noise; level n >= 1 draws noise with
  *       the step index n; faces are applied in the order y, z, x.
+ *   R17 centerline (Sec. "Centerline Boundary Condition"), a j- face whose
+ *       points are the degenerate axis of a polar grid (J^-1 = 0 there):
+ *       its conserved variables are the azimuthal average (k = 0, 1, ...
+ *       in order) of the unscaled conserved variables of the adjacent ring
+ *       j = 1, the same at every k; the state is stored there unscaled
+ *       (state scale 1 instead of J^-1 = 0), and point quantities that
+ *       need d xi/d x (spectral radii, chain rule) take J = 1 there; the
+ *       filter width and the interface J^-1 averages use the true J^-1.
+ *       lambda-bar is evaluated in its product form lambda_a +
+ *       (lambda_a lambda_b)^1/2 + (lambda_a lambda_d)^1/2, which is the
+ *       paper's expression for lambda_a > 0 and its limit 0 at lambda_a = 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -61,7 +72,7 @@
 
 #define NF 5
 
-enum { BC_PERIODIC = 0, BC_FARFIELD = 1, BC_INFLOW_JET = 2, BC_EXIT = 3 };
+enum { BC_PERIODIC = 0, BC_FARFIELD = 1, BC_INFLOW_JET = 2, BC_EXIT = 3, BC_CENTERLINE = 4 };
 
 typedef struct {
     int n[3];
@@ -255,16 +266,20 @@ static void cons_from_prim(const Params *P, double rho, double u, double v, doub
     Q[4] = p / (P->gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
 }
 
+/* Scale of the stored state at a point: J^-1, or 1 on the degenerate
+ * centerline where J^-1 = 0 (reading R17). */
+static double state_scale(double Jinv) { return Jinv > 0.0 ? Jinv : 1.0; }
+
 /* Unscaled Q at point index p from the stored Qhat = J^-1 Q. */
 static void load_Q(const Grid *g, const double *m, const double *qhat, long p, double Q[5])
 {
-    double Jinv = m[9 * g->N + p];
+    double Jinv = state_scale(m[9 * g->N + p]);
     for (int f = 0; f < NF; f++) Q[f] = qhat[f * g->N + p] / Jinv;
 }
 
 static void store_Q(const Grid *g, const double *m, double *qhat, long p, const double Q[5])
 {
-    double Jinv = m[9 * g->N + p];
+    double Jinv = state_scale(m[9 * g->N + p]);
     for (int f = 0; f < NF; f++) qhat[f * g->N + p] = Jinv * Q[f];
 }
 
@@ -337,7 +352,7 @@ static void compute_gradients_and_sgs(const Grid *g, const Params *P, const doub
         for (int i = 0; i < 3; i++) {
             double d[3] = {W->grad[(3 * i + 0) * g->N + p], W->grad[(3 * i + 1) * g->N + p],
                            W->grad[(3 * i + 2) * g->N + p]};
-            chain_rule(mc, m[9 * g->N + p], d, gu[i]);
+            chain_rule(mc, state_scale(m[9 * g->N + p]), d, gu[i]);
         }
         strain(gu, S);
         W->musgs[p] = smagorinsky(P, W->rho[p], m[9 * g->N + p], S);
@@ -353,7 +368,7 @@ static void compute_gradients_and_sgs(const Grid *g, const Params *P, const doub
 static void inviscid_flux(const Grid *g, const double *m, const double *qhat, const Work *W, int a,
                           long p, double F[5])
 {
-    double Jinv = m[9 * g->N + p];
+    double Jinv = state_scale(m[9 * g->N + p]);
     double mx = m[(3 * a + 0) * g->N + p], my = m[(3 * a + 1) * g->N + p],
            mz = m[(3 * a + 2) * g->N + p];
     double JU = mx * W->u[p] + my * W->v[p] + mz * W->w[p];
@@ -375,7 +390,7 @@ static void inviscid_flux(const Grid *g, const double *m, const double *qhat, co
 static double spectral_radius(const Grid *g, const Params *P, const double *m, const Work *W, int a,
                               long p)
 {
-    double Jinv = m[9 * g->N + p];
+    double Jinv = state_scale(m[9 * g->N + p]);
     double mx = m[(3 * a + 0) * g->N + p] / Jinv, my = m[(3 * a + 1) * g->N + p] / Jinv,
            mz = m[(3 * a + 2) * g->N + p] / Jinv;
     double U = mx * W->u[p] + my * W->v[p] + mz * W->w[p];
@@ -384,14 +399,15 @@ static double spectral_radius(const Grid *g, const Params *P, const double *m, c
 }
 
 /* Anisotropic scaling lambda-bar_a = lambda_a [1 + (lambda_b/lambda_a)^0.5 +
- * (lambda_d/lambda_a)^0.5] with b, d the other two axes. */
+ * (lambda_d/lambda_a)^0.5] with b, d the other two axes, evaluated as
+ * lambda_a + (lambda_a lambda_b)^0.5 + (lambda_a lambda_d)^0.5 (reading R17). */
 static double lambda_bar(const Grid *g, const Params *P, const double *m, const Work *W, int a,
                          long p)
 {
     double la = spectral_radius(g, P, m, W, a, p);
     double lb = spectral_radius(g, P, m, W, (a + 1) % 3, p);
     double ld = spectral_radius(g, P, m, W, (a + 2) % 3, p);
-    return la * (1.0 + pow(lb / la, 0.5) + pow(ld / la, 0.5));
+    return la + sqrt(la * lb) + sqrt(la * ld);
 }
 
 /* Pressure sensor along axis a at point q (reading R5). */
@@ -704,6 +720,20 @@ static void apply_bc(const Grid *g, const Params *P, const double *m, double *qh
         int b = (a + 1) % 3, d = (a + 2) % 3;
         for (int side = 0; side < 2; side++) {
             int type = g->bc[2 * a + side];
+            if (type == BC_CENTERLINE) {
+                /* j- face on the axis: azimuthal (k) average of the ring j = 1 */
+                for (int i = 0; i < g->n[0]; i++) {
+                    double avg[5] = {0, 0, 0, 0, 0};
+                    for (int k = 0; k < g->n[2]; k++) {
+                        double Qe[5];
+                        load_Q(g, m, qhat, lin(g, i, 1, k), Qe);
+                        for (int f = 0; f < NF; f++) avg[f] += Qe[f];
+                    }
+                    for (int f = 0; f < NF; f++) avg[f] /= (double)g->n[2];
+                    for (int k = 0; k < g->n[2]; k++) store_Q(g, m, qhat, lin(g, i, 0, k), avg);
+                }
+                continue;
+            }
             int fa = side == 0 ? 0 : g->n[a] - 1;
             int ea = side == 0 ? 1 : g->n[a] - 2;
             double sgn = side == 0 ? -1.0 : 1.0;

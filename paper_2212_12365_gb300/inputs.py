@@ -17,7 +17,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-BC_PERIODIC, BC_FARFIELD, BC_INFLOW_JET, BC_EXIT = 0, 1, 2, 3
+BC_PERIODIC, BC_FARFIELD, BC_INFLOW_JET, BC_EXIT, BC_CENTERLINE = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -265,6 +265,27 @@ def cylinder_points(r: float, n_theta: int, n_x: int, x0: float, x1: float) -> n
     xs = np.linspace(x0, x1, n_x)
     X, TH = np.meshgrid(xs, th, indexing="ij")
     return np.stack([X.reshape(-1), (r * np.cos(TH)).reshape(-1), (r * np.sin(TH)).reshape(-1)])
+
+
+def polar_jet_grid(ni: int, nj: int, nk: int, Lx: float, R: float, growth: float = 3.0) -> GridSpec:
+    """The paper's jet mesh topology (Sec. "Mesh Generation"): a 2-D (x, r) mesh
+    rotated about the x axis.  i: axial, uniform on [0, Lx]; j: radial from the
+    centerline r = 0 (a degenerate line, J^-1 = 0) to R, spacing growing
+    geometrically-like with r(t) = R t (1 + growth t) / (1 + growth); k:
+    azimuthal, nk unique angles 2 pi k / nk (periodic, no duplicated point).
+    Faces: jet inflow at x = 0, exit at x = Lx, centerline at j = 0, far field
+    at r = R."""
+    x1 = np.linspace(0.0, Lx, ni)
+    t = np.linspace(0.0, 1.0, nj)
+    r1 = R * t * (1.0 + growth * t) / (1.0 + growth)
+    th = 2.0 * np.pi * np.arange(nk) / nk
+    K, J, Iax = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+    x = x1[Iax].reshape(-1)
+    y = (r1[J] * np.cos(th[K])).reshape(-1)
+    z = (r1[J] * np.sin(th[K])).reshape(-1)
+    return GridSpec(x=x, y=y, z=z, dims=(ni, nj, nk), periodic=(0, 0, 1),
+                    shift=np.zeros((3, 3)),
+                    bc=(BC_INFLOW_JET, BC_EXIT, BC_CENTERLINE, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC))
 
 
 def curved_periodic_grid(n: tuple, L: float = 1.0, A: float = 0.04) -> GridSpec:
