@@ -56,6 +56,8 @@ WORKLOADS = {
     "jet-768x384x192": (I.jet_large, "fp32"),
     "jet-48x32x32": (I.jet_small, "fp64"),
     "jet-192x128x72": (I.jet_medium, "fp64"),
+    # the paper's polar mesh with the centerline condition (not a product grid)
+    "polar-384x192x192": (I.polar_jet_paper_scale, "fp64"),
 }
 
 
@@ -346,7 +348,8 @@ def run_ours(args):
                "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8, "steps": ke}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not batch:
+    # (a k-slab of a polar mesh would cut its azimuthal period: no CPU sample there)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not batch and not spec.periodic[2]:
         cpu = cpu_baseline(spec, fp)
     secondary = None
     if rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64" and not args.no_fp32:

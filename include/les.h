@@ -56,6 +56,10 @@ extern "C" {
 #define LES_BC_FARFIELD 1   /* Sec. "Far Field Boundary", Riemann invariants */
 #define LES_BC_INFLOW_JET 2 /* Sec. "Entrance Boundary", supersonic jet + far field */
 #define LES_BC_EXIT 3       /* Sec. "Exit Boundary Condition" */
+#define LES_BC_CENTERLINE 4 /* Sec. "Centerline Boundary Condition": the j- face is the
+                               degenerate axis of a polar mesh (J^-1 = 0 allowed there; k
+                               must be periodic): its state is the azimuthal mean of the
+                               ring j = 1, stored unscaled */
 
 /* Storage / arithmetic precision of the stencil path. Metrics and the
  * Jacobian are always computed in FP64; diagnostics sum in FP64. */

@@ -46,6 +46,8 @@ constexpr int DIAG_BLOCKS = 608; // blocks of the diagnostics reduction (fixed o
 struct les_handle {
     int prec = LES_FP64;        // LES_FP64 or LES_FP32 (storage and arithmetic)
     bool sep = false;           // FP32 separable-metric stage (LES_FP32_SEPARABLE)
+    bool centerline = false;    // some jet has a centerline face
+    int max_ni = 0;
     int njets = 0;
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;
@@ -127,8 +129,10 @@ static std::string validate(const les_grid_desc *g, const les_params *p)
     }
     for (int f = 0; f < 6; ++f) {
         int t = g->face_bc[f];
-        if (t < LES_BC_PERIODIC || t > LES_BC_EXIT) return "unknown face boundary condition";
+        if (t < LES_BC_PERIODIC || t > LES_BC_CENTERLINE) return "unknown face boundary condition";
         if (t == LES_BC_INFLOW_JET && f != 0) return "INFLOW_JET is allowed on the i- face only";
+        if (t == LES_BC_CENTERLINE && f != 2) return "CENTERLINE is allowed on the j- face only";
+        if (t == LES_BC_CENTERLINE && !g->periodic[2]) return "CENTERLINE needs a periodic (azimuthal) k axis";
     }
     if (g->face_bc[0] == LES_BC_INFLOW_JET && !(p->mach_j >= 1.0))
         return "INFLOW_JET needs a supersonic jet (mach_j >= 1)";
@@ -320,10 +324,12 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
     std::vector<double> jv((size_t)J.fs);
     CK(cudaMemcpyAsync(jv.data(), J.jinv64, (size_t)J.fs * 8, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    const bool axis = J.bc[2] == LES_BC_CENTERLINE;
     for (int k = 0; k < J.n[2]; ++k)
         for (int j = 0; j < J.n[1]; ++j)
             for (int i = 0; i < J.n[0]; ++i) {
                 double v = jv[((size_t)k * J.n[1] + j) * J.pitch + i];
+                if (axis && j == 0 && v == 0.0) continue; // the degenerate axis of a polar mesh
                 if (!(v > 0.0) || !std::isfinite(v))
                     return fail(h, LES_ERR_ARG, "non-positive or non-finite cell volume J^-1 at (" +
                                                     std::to_string(i) + "," + std::to_string(j) +
@@ -434,6 +440,8 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
         J.off = jets_bytes;
         jets_bytes += align_up(J.bytes, 256);
         maxN = std::max(maxN, J.N);
+        if (J.bc[2] == LES_BC_CENTERLINE) h->centerline = true;
+        h->max_ni = std::max(h->max_ni, J.n[0]);
     }
     h->nblk_diag = DIAG_BLOCKS;
     GlobalPlan GP = plan_global(njets, sizeof(JetDev<real>), h->nblk_diag, maxN);
@@ -627,6 +635,10 @@ static int bc_pass(les_handle *h, const BlockMap bcm[3], const JetDev<real> *jet
     static const int order[3] = {1, 2, 0};
     for (int oi = 0; oi < 3; ++oi) {
         int a = order[oi];
+        if (a == 1 && h->centerline) {
+            launch_centerline<real>(jets, bcm[1].njets, h->max_ni, dst, st);
+            h->launches_per_step++;
+        }
         if (bcm[a].total == 0) continue;
         Launch<real>::bc(jets, bcm[a], a, dst, h->d_level, grid_cap(h, bcm[a].total), st);
         h->launches_per_step++;
@@ -679,6 +691,12 @@ template <typename real> static int record_step(les_handle *h, cudaStream_t st, 
             h->launches_per_step += 1;
             for (int oi = 0; oi < 3; ++oi) {
                 int a = order[oi];
+                if (a == 1 && h->centerline) {
+                    T.begin(LES_KERNEL_BC);
+                    launch_centerline<real>(jets, h->njets, h->max_ni, dst_of[s], st);
+                    T.end();
+                    h->launches_per_step++;
+                }
                 if (h->bcm[a].total == 0) continue;
                 T.begin(LES_KERNEL_BC);
                 Launch<real>::bc(jets, h->bcm[a], a, dst_of[s], h->d_level, grid_cap(h, h->bcm[a].total), st);
@@ -702,6 +720,12 @@ template <typename real> static int record_step(les_handle *h, cudaStream_t st, 
         h->launches_per_step += 4;
         for (int oi = 0; oi < 3; ++oi) {
             int a = order[oi];
+            if (a == 1 && h->centerline) {
+                T.begin(LES_KERNEL_BC);
+                launch_centerline<real>(jets, h->njets, h->max_ni, dst_of[s], st);
+                T.end();
+                h->launches_per_step++;
+            }
             if (h->bcm[a].total == 0) continue;
             T.begin(LES_KERNEL_BC);
             Launch<real>::bc(jets, h->bcm[a], a, dst_of[s], h->d_level, grid_cap(h, h->bcm[a].total), st);

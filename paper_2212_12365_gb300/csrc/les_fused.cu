@@ -100,6 +100,9 @@ __device__ __forceinline__ int gidx(int g, int n, int per)
 // Square root of a strictly positive argument through the hardware
 // reciprocal square root (max. 2 ulp): x * rsqrt(x).
 __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+// The same for x >= 0 (0 -> 0): a spectral radius vanishes on the axis of a
+// polar mesh, so the products of lambda-bar can be zero.
+__device__ __forceinline__ float sqrt_nonneg(float x) { return x * rsqrtf(fmaxf(x, 1.17549435e-38f)); }
 
 // Asynchronous 4-byte global -> shared copy (completes without the issuing
 // thread waiting; cp_async_wait_all() waits for all of this thread's copies).
@@ -677,8 +680,8 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                         lam[a] = (fabsf(JU) + sT * nrm[a]) * rjG;
                     }
                 }
-                const float s01 = sqrt_pos(lam[0] * lam[1]), s02 = sqrt_pos(lam[0] * lam[2]),
-                            s12 = sqrt_pos(lam[1] * lam[2]);
+                const float s01 = sqrt_nonneg(lam[0] * lam[1]), s02 = sqrt_nonneg(lam[0] * lam[2]),
+                            s12 = sqrt_nonneg(lam[1] * lam[2]);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) S.GD[(rG * 3 + a) * N1 + c1] = dd[a].d;
                 S.GC[(rG * 2 + 0) * N1 + c1] = make_float4(mu * FP.inv_Re + mus, mu * FP.kap_mol + mus * FP.kap_sgs,

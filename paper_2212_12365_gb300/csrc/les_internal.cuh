@@ -110,6 +110,11 @@ __host__ __device__ __forceinline__ long long lidx(const JetDev<real> &J, int i,
     return ((long long)k * J.n[1] + j) * J.pitch + i;
 }
 
+// Scale of the stored state Qhat = s Q at a point: J^-1, or 1 on the
+// degenerate axis of a polar mesh (centerline face), where J^-1 = 0 and the
+// state is kept unscaled (Sec. "Centerline Boundary Condition").
+__host__ __device__ __forceinline__ double state_scale(double jinv) { return jinv > 0.0 ? jinv : 1.0; }
+
 __host__ __device__ __forceinline__ int wrapi(int a, int n)
 {
     a %= n;
@@ -242,6 +247,12 @@ template <typename real> struct Launch {
                       int every, const long long *level, const long long *base, real *out,
                       int capacity, cudaStream_t st);
 };
+
+// Centerline faces (j- face of type LES_BC_CENTERLINE) of jets [0, njets):
+// the conserved variables of every axis point are the azimuthal mean of the
+// adjacent ring j = 1.
+template <typename real>
+void launch_centerline(const JetDev<real> *jets, int njets, int max_ni, int dst, cudaStream_t st);
 
 void launch_diag_final(const double *partials, int nblocks, double *out, cudaStream_t st);
 void launch_step_advance(long long *level, cudaStream_t st);

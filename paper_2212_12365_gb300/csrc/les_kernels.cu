@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long 
         q[2] = (int)(p / ((long long)ni * nj));
         const long long o = ((long long)q[2] * nj + q[1]) * pitch + q[0];
         const double jinv = met[MET_JINV * fs + o];
-        met[MET_J * fs + o] = 1.0 / jinv;
+        met[MET_J * fs + o] = 1.0 / state_scale(jinv);
         for (int a = 0; a < 3; ++a) {
             int r[3] = {q[0], q[1], q[2]};
             if (per[a]) r[a] = (q[a] + 1) % n[a];
@@ -206,12 +206,13 @@ __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long 
             const long long oR = ((long long)r[2] * nj + r[1]) * pitch + r[0];
             const double jb = 0.5 * (jinv + met[MET_JINV * fs + oR]);
             met[(MET_JB + a) * fs + o] = jb;
-            met[(MET_RJB + a) * fs + o] = 1.0 / jb;
+            // an interface along the degenerate axis has no volume: zero weights
+            met[(MET_RJB + a) * fs + o] = jb > 0.0 ? 1.0 / jb : 0.0;
             const double mx = met[(3 * a) * fs + o], my = met[(3 * a + 1) * fs + o],
                          mz = met[(3 * a + 2) * fs + o];
             met[(MET_NORM + a) * fs + o] = sqrt(mx * mx + my * my + mz * mz);
             if (iface_tables) {
-                const double rjb = 1.0 / jb;
+                const double rjb = jb > 0.0 ? 1.0 / jb : 0.0;
                 double A[9];
                 for (int b = 0; b < 3; ++b)
                     for (int c = 0; c < 3; ++c) {
@@ -364,6 +365,30 @@ template <typename T> __device__ void bc_exit(const BcK<T> &k, const T Qe[5], co
     Qf[4] = rho * (ei + T(0.5) * (e.u[0] * e.u[0] + e.u[1] * e.u[1] + e.u[2] * e.u[2]));
 }
 
+// Centerline (Sec. "Centerline Boundary Condition"): one thread per (axial
+// station i, conserved variable f) of a jet whose j- face is the axis sums the
+// unscaled ring j = 1 over k in index order (deterministic, the same sum for
+// every axis point) and writes the mean, unscaled (state scale 1), to all
+// azimuthal copies of the axis point (i, 0, k).
+template <typename real>
+__global__ void __launch_bounds__(BLOCK) k_centerline(const JetDev<real> *__restrict__ jets, int dst)
+{
+    const JetDev<real> &J = jets[blockIdx.y];
+    if (J.bc[2] != LES_BC_CENTERLINE) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 5 * J.n[0]) return;
+    const int i = t / 5, f = t % 5;
+    const long long fs = J.fs;
+    real *Q = J.q[dst] + f * fs;
+    double sum = 0.0;
+    for (int k = 0; k < J.n[2]; ++k) {
+        const long long o = lidx(J, i, 1, k);
+        sum += (double)Q[o] / state_scale(J.jinv64[o]);
+    }
+    const double avg = sum / (double)J.n[2];
+    for (int k = 0; k < J.n[2]; ++k) Q[lidx(J, i, 0, k)] = (real)avg;
+}
+
 // SplitMix64: output number n of the generator seeded with `seed`.
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
                                                          unsigned long long n)
@@ -412,7 +437,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         }
         const T rn = rsqrt(nn);
         for (int c = 0; c < 3; ++c) n[c] *= rn;
-        const T jinvE = (T)J.jinv64[E], jinvF = (T)J.jinv64[F];
+        const T jinvE = (T)state_scale(J.jinv64[E]), jinvF = (T)state_scale(J.jinv64[F]);
         const T rjE = T(1) / jinvE;
         T Qe[5], Qf[5];
         for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] * rjE;
@@ -487,7 +512,7 @@ __global__ void __launch_bounds__(BLOCK) k_set_state(const JetDev<real> *__restr
         } else {
             for (int f = 0; f < 5; ++f) Qc[f] = v[f];
         }
-        const double jinv = J.jinv64[lp];
+        const double jinv = state_scale(J.jinv64[lp]);
         for (int f = 0; f < 5; ++f) Q[f * J.fs + lp] = (real)(jinv * Qc[f]);
     }
 }
@@ -507,7 +532,7 @@ __global__ void __launch_bounds__(BLOCK) k_get_state(const JetDev<real> *__restr
         double v[5];
         for (int f = 0; f < 5; ++f) v[f] = (double)Q[f * J.fs + lp];
         if (kind != LES_STATE_RAW) {
-            const double jinv = J.jinv64[lp];
+            const double jinv = state_scale(J.jinv64[lp]);
             for (int f = 0; f < 5; ++f) v[f] /= jinv;
             if (kind == LES_STATE_PRIMITIVE) {
                 Prim64 s = prim_of(v, J.gamma);
@@ -539,7 +564,7 @@ __global__ void __launch_bounds__(BLOCK) k_dt_max(const JetDev<real> *__restrict
         int q[3];
         if (lp < J.npts_pad && point_of(J, lp, q)) {
             const long long fs = J.fs;
-            double rj = 1.0 / (double)J.met[MET_JINV * fs + lp];
+            double rj = 1.0 / state_scale((double)J.met[MET_JINV * fs + lp]);
             double u = J.prim[P_U * fs + lp], v = J.prim[P_V * fs + lp], w = J.prim[P_W * fs + lp];
             double c = sqrt((double)J.prim[P_T * fs + lp]);
             for (int a = 0; a < 3; ++a) {
@@ -715,7 +740,7 @@ __global__ void __launch_bounds__(BLOCK) k_probe(const JetDev<real> *__restrict_
                 wgt *= up ? t[a] : 1.0 - t[a];
             }
             long long p = lidx(J, r[0], r[1], r[2]);
-            double jinv = J.jinv64[p];
+            double jinv = state_scale(J.jinv64[p]);
             double Q[5];
             for (int f = 0; f < 5; ++f) Q[f] = (double)J.q[0][f * fs + p] / jinv;
             Prim64 pr = prim_of(Q, g);
@@ -774,6 +799,15 @@ void Launch<real>::convert_metrics(const double *met64, long long fs64, real *me
 {
     k_convert_metrics<real><<<grid_for(npad), BLOCK, 0, st>>>(met64, fs64, met, fs, npad);
 }
+
+template <typename real>
+void launch_centerline(const JetDev<real> *jets, int njets, int max_ni, int dst, cudaStream_t st)
+{
+    dim3 grid((5 * max_ni + BLOCK - 1) / BLOCK, njets);
+    k_centerline<real><<<grid, BLOCK, 0, st>>>(jets, dst);
+}
+template void launch_centerline<float>(const JetDev<float> *, int, int, int, cudaStream_t);
+template void launch_centerline<double>(const JetDev<double> *, int, int, int, cudaStream_t);
 
 template <typename real>
 void Launch<real>::bc(const JetDev<real> *jets, BlockMap bm, int axis, int dst,

@@ -134,6 +134,13 @@ def jet_large() -> tuple[GridSpec, FlowParams]:
             FlowParams(mach_j=1.4, TR=2.0, Re=1.0e5, Cs=0.17, cfl=0.5, seed=5))
 
 
+def polar_jet_paper_scale() -> tuple[GridSpec, FlowParams]:
+    """The paper's mesh topology at its size (~14 M points): 384 axial x 192
+    radial x 192 azimuthal, 30D long, radius 12D, centerline at j = 0."""
+    return (polar_jet_grid(384, 192, 192, 30.0, 12.0),
+            FlowParams(mach_j=1.4, TR=1.0, Re=1.0e5, Cs=0.17, cfl=0.5, seed=6))
+
+
 def jet_slab(spec: GridSpec, k0: int, k1: int) -> GridSpec:
     """Planes k0..k1-1 of a grid (a bounded sample of a larger workload)."""
     ni, nj, nk = spec.dims

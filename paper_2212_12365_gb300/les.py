@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libles.so")
 
 LES_OK, LES_ERR_ARG, LES_ERR_OOM, LES_ERR_CUDA, LES_ERR_NONFINITE, LES_ERR_TIMEOUT, LES_ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6)
-LES_BC_PERIODIC, LES_BC_FARFIELD, LES_BC_INFLOW_JET, LES_BC_EXIT = 0, 1, 2, 3
+LES_BC_PERIODIC, LES_BC_FARFIELD, LES_BC_INFLOW_JET, LES_BC_EXIT, LES_BC_CENTERLINE = 0, 1, 2, 3, 4
 LES_FP64, LES_FP32, LES_FP32_SEPARABLE = 0, 1, 2
 LES_STATE_CONSERVED, LES_STATE_PRIMITIVE, LES_STATE_RAW = 0, 1, 2
 (LES_FIELD_MU_SGS, LES_FIELD_MU, LES_FIELD_P, LES_FIELD_T, LES_FIELD_LAMBDA_XI,
