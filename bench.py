@@ -205,10 +205,11 @@ def run_reference(args):
 def precision_form(args, spec, fp, les, torch, fp64_value):
     """FP32 storage/arithmetic on the same grid (metrics and sums in FP64): its
     rate, speedup over the FP64 path, and relative L2 per field against the FP64
-    path after the same number of steps from the ambient start."""
+    path after 100 steps from the ambient start (the accuracy criterion of the
+    FP32 form; more if the timed run is longer)."""
     forms = {}
     states = {}
-    steps = args.warmup + args.steps
+    steps = max(100, args.warmup + args.steps)
     names = {les.LES_FP32: "fp32", les.LES_FP32_SEPARABLE: "fp32-sep"}
     for prec in (les.LES_FP32, les.LES_FP32_SEPARABLE, les.LES_FP64):
         s = les.Solver(spec, fp, prec)
@@ -225,6 +226,7 @@ def precision_form(args, spec, fp, les, torch, fp64_value):
             ms = e0.elapsed_time(e1)
             forms[prec] = {"precision": names[prec], "value": spec.N * 5 * args.steps / (ms / 1e3),
                            "ms_per_step": ms / args.steps, "stage": les.les_describe(s.h)}
+            s.step(steps - args.warmup - args.steps)
         else:
             s.step(steps)
         states[prec] = s.get_state(les.LES_STATE_CONSERVED)
