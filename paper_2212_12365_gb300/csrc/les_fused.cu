@@ -688,7 +688,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                                                            dd[0].nu, lam[0] + s01 + s02);
                 S.GC[(rG * 2 + 1) * N1 + c1] = make_float4(dd[1].nu, lam[1] + s01 + s12, dd[2].nu, lam[2] + s02 + s12);
             }
-            __syncthreads();
+            // No barrier here: the interfaces below read the R1 tables of plane
+            // kG only in this thread's own column (the zeta neighbour), written
+            // just above by this thread; everything they read from other
+            // threads (plane kU tables, the point ring) was written before the
+            // previous iteration's closing barrier, and the phase writes only
+            // plane-kG slots, which no interface of this iteration reads.
             if constexpr (SEP) {
                 // next plane's state and the next update's Q(0), in flight
                 // during the interface arithmetic
