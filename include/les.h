@@ -218,6 +218,16 @@ int les_debug_field(les_handle *h, int jet, int field, double *out);
 #define LES_KERNEL_KINDS 6
 int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts);
 
+/* Work decomposition of the fused FP32 stage (LES_FP32, LES_FP32_SEPARABLE
+ * handles): ty = 8 or 16 grid rows per CTA tile (32 x ty threads), kc >= 1
+ * planes per k-chunk item, or kc = 0 for the balanced form (every CTA of the
+ * persistent grid takes one contiguous, equal share of all tile-planes).  By
+ * default the first les_step picks the fastest choice by timing them
+ * (autotuner); this call sets it instead and disables the tuning for the
+ * handle.  Results are bit-identical for every choice.  Errors: LES_ERR_ARG
+ * (FP64 handle, bad ty or kc). */
+int les_set_fused_tiling(les_handle *h, int ty, int kc);
+
 /* Kernel launches issued by the most recent les_step call (all steps). */
 int64_t les_last_launch_count(les_handle *h);
 

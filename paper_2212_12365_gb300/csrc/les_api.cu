@@ -77,6 +77,7 @@ struct les_handle {
     FusedJet *d_fj = nullptr, *d_fj1 = nullptr;
     std::vector<FusedJet> fj;
     int fused_ty = 16;
+    bool fused_balanced = false;
     int fused_items = 0;
     bool tuned = false;
     std::string tune_note;
@@ -356,7 +357,8 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
 // Interior output range length of one axis.
 static int out_len(const JetHost &J, int a) { return J.per[a] ? J.n[a] : J.n[a] - 2; }
 
-// Work-list tables of the fused stage for tile height ty and k-chunk kc.
+// Work-list tables of the fused stage for tile height ty and k-chunk kc
+// (kc = 0: balanced form, items are tile-planes split evenly over the grid).
 static int set_fused_tiling(les_handle *h, int ty, int kc)
 {
     int acc = 0;
@@ -366,14 +368,20 @@ static int set_fused_tiling(les_handle *h, int ty, int kc)
         const JetHost &J = h->J[j];
         F.nbx = (out_len(J, 0) + 29) / 30;
         F.nby = (out_len(J, 1) + ty - 3) / (ty - 2);
-        F.kc = std::max(1, std::min(kc, out_len(J, 2)));
-        F.nkc = (out_len(J, 2) + F.kc - 1) / F.kc;
+        if (kc == 0) {
+            F.kc = 0;
+            F.nkc = out_len(J, 2); // planes per column: the items are tile-planes
+        } else {
+            F.kc = std::max(1, std::min(kc, out_len(J, 2)));
+            F.nkc = (out_len(J, 2) + F.kc - 1) / F.kc;
+        }
         F.item0 = acc;
         acc += F.nbx * F.nby * F.nkc;
         one[j] = F;
         one[j].item0 = 0;
     }
     h->fused_ty = ty;
+    h->fused_balanced = kc == 0;
     h->fused_items = acc;
     CK(cudaMemcpyAsync(h->d_fj, h->fj.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_fj1, one.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
@@ -393,10 +401,11 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     const int items = jet < 0 ? h->fused_items : items_of(h->fj[jet]);
     const int grid = std::max(1, std::min(items, h->nsm * (h->fused_ty == 16 ? 1 : 2)));
     if (jet >= 0) jets += jet;
+    const int bal = h->fused_balanced ? 1 : 0;
     if (h->fused_ty == 16)
-        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, st);
+        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal, st);
     else
-        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, st);
+        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal, st);
 }
 
 template <typename real>
@@ -945,7 +954,7 @@ static int autotune_fused(les_handle *h)
     auto it = g_tune_cache.find(key);
     if (it == g_tune_cache.end()) {
         const int tys[2] = {16, 8};
-        const int kcs[6] = {8, 16, 24, 48, 96, 100000};
+        const int kcs[7] = {8, 16, 24, 48, 96, 100000, 0}; // 0: balanced tile-plane ranges
         float best = 1e30f;
         std::pair<int, int> pick{8, 48};
         cudaEvent_t e0, e1;
@@ -973,8 +982,9 @@ static int autotune_fused(les_handle *h)
         cudaEventDestroy(e1);
         it = g_tune_cache.emplace(key, pick).first;
     }
-    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" + std::to_string(it->second.second) +
-                   " (tuned over ty {16,8} x kc {8,16,24,48,96,all})";
+    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" +
+                   (it->second.second == 0 ? std::string("balanced") : std::to_string(it->second.second)) +
+                   " (tuned over ty {16,8} x kc {8,16,24,48,96,all,balanced})";
     return set_fused_tiling(h, it->second.first, it->second.second);
 }
 
@@ -1065,6 +1075,23 @@ extern "C" int les_debug_field(les_handle *h, int jet, int field, double *out)
 // ---------------------------------------------------------------------------
 // Surface probe
 // ---------------------------------------------------------------------------
+
+extern "C" int les_set_fused_tiling(les_handle *h, int ty, int kc)
+{
+    if (!h) return LES_ERR_ARG;
+    if (h->prec != LES_FP32) return fail(h, LES_ERR_ARG, "the fused tiling applies to FP32 handles");
+    if ((ty != 8 && ty != 16) || kc < 0) return fail(h, LES_ERR_ARG, "ty must be 8 or 16 and kc >= 0");
+    int rc = set_fused_tiling(h, ty, kc);
+    if (rc) return rc;
+    h->tuned = true;
+    h->tune_note = "ty=" + std::to_string(ty) + " kc=" + (kc == 0 ? std::string("balanced") : std::to_string(kc)) +
+                   " (set by the caller)";
+    if (h->gexec) { // the captured step holds the old work list
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return LES_OK;
+}
 
 extern "C" int les_probe_surface(les_handle *h, const double *xyz, int npts, int every_n, void *dev_out,
                                  int out_capacity_frames)

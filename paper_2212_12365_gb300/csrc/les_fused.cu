@@ -400,7 +400,8 @@ __device__ __forceinline__ D3 deriv_end(int t, const float4 &a1, const float2 &b
 template <int TY, bool SEP>
 __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
-            int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only)
+            int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only,
+            int balanced)
 {
     using G_ = Geo<TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -412,32 +413,56 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     const int c2 = (ty + 1) * C2X + (tx + 1);
     const int c1 = tid;
 
-    for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
+    // Work cursor: items (jet, tile, k-chunk) strided over the grid, or, in the
+    // balanced form, the CTA's contiguous share of all tile-planes (jet-major,
+    // tile, then plane), cut into one column piece per tile it touches; a
+    // piece starting mid-column recomputes its first zeta flux, so the result
+    // does not depend on where the cuts fall.
+    int item = blockIdx.x, w = 0, wend = 0;
+    if (balanced) {
+        w = (int)(((long long)total_items * blockIdx.x) / gridDim.x);
+        wend = (int)(((long long)total_items * (blockIdx.x + 1)) / gridDim.x);
+    }
+    while (balanced ? w < wend : item < total_items) {
+        const int key = balanced ? w : item;
         int jet = 0;
         {
             int lo = 0, hi = njets;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (fj[mid].item0 <= item) lo = mid; else hi = mid;
+                if (fj[mid].item0 <= key) lo = mid; else hi = mid;
             }
             jet = lo;
         }
         const JetDev<float> &J = jets[jet];
         const FusedJet &F = fj[jet];
         const FusedParams &FP = F.fp;
-        int r = item - F.item0;
-        const int bx = r % F.nbx;
-        r /= F.nbx;
-        const int by = r % F.nby;
-        const int kc = r / F.nby;
         const int ni = J.n[0], nj = J.n[1], nk = J.n[2];
         const int pi = J.per[0], pj = J.per[1], pk = J.per[2];
         const int ilo = pi ? 0 : 1, ihi = pi ? ni : ni - 1;
         const int jlo = pj ? 0 : 1, jhi = pj ? nj : nj - 1;
         const int klo = pk ? 0 : 1, khi = pk ? nk : nk - 1;
+        int bx, by, k0, k1;
+        if (balanced) {
+            const int np = khi - klo; // planes per column (F.nkc)
+            const int r = key - F.item0;
+            const int tile = r / np, pl = r - tile * np;
+            bx = tile % F.nbx;
+            by = tile / F.nbx;
+            k0 = klo + pl;
+            k1 = klo + min(np, pl + (wend - w));
+            w += k1 - k0;
+        } else {
+            int r = key - F.item0;
+            bx = r % F.nbx;
+            r /= F.nbx;
+            by = r % F.nby;
+            const int kc = r / F.nby;
+            k0 = klo + kc * F.kc;
+            k1 = min(k0 + F.kc, khi);
+            item += gridDim.x;
+        }
         const int i0 = ilo + bx * (FX - 2), j0 = jlo + by * (TY - 2);
-        const int k0 = klo + kc * F.kc;
-        const int k1 = min(k0 + F.kc, khi);
         const int ib = i0 - 1, jb = j0 - 1;
         const long long fs = J.fs;
         const long long plane = (long long)nj * J.pitch;
@@ -832,15 +857,15 @@ template <int TY> int fused_prepare()
 
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid, int src,
-                  int dst, int stage, const double *dt, int rhs_only, int separable, cudaStream_t st)
+                  int dst, int stage, const double *dt, int rhs_only, int separable, int balanced, cudaStream_t st)
 {
     dim3 block(FX, TY);
     if (separable)
         k_fused<TY, true><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                              rhs_only);
+                                                              rhs_only, balanced);
     else
         k_fused<TY, false><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                               rhs_only);
+                                                               rhs_only, balanced);
 }
 
 template size_t fused_smem_bytes<16>();
@@ -848,8 +873,8 @@ template size_t fused_smem_bytes<8>();
 template int fused_prepare<16>();
 template int fused_prepare<8>();
 template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                               const double *, int, int, cudaStream_t);
+                               const double *, int, int, int, cudaStream_t);
 template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                              const double *, int, int, cudaStream_t);
+                              const double *, int, int, int, cudaStream_t);
 
 } // namespace les

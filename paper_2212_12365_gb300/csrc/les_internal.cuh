@@ -190,11 +190,13 @@ struct FusedParams {
 };
 
 // Work-list entry of one jet for the fused stage kernel: items
-// [item0, item0 + nbx*nby*nkc) are its (tile x, tile y, k-chunk) triples.
+// [item0, item0 + nbx*nby*nkc) are its (tile x, tile y, k-chunk) triples.  In
+// the balanced form (kc == 0) the items are its tile-planes, nkc = the number
+// of planes per column, and every CTA takes one contiguous range of them.
 struct FusedJet {
     int item0;
     int nbx, nby, nkc;
-    int kc;                 // planes per k-chunk
+    int kc;                 // planes per k-chunk (0: balanced form)
     FusedParams fp;
     // separable form (Cartesian-product grid): per axis a, for each index,
     // (h, 1/h, h^(2/3), 0) with h the derivative of coordinate a along axis a
@@ -208,7 +210,8 @@ template <int TY> size_t fused_smem_bytes();
 template <int TY> int fused_prepare();
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
-                  int src, int dst, int stage, const double *dt, int rhs_only, int separable, cudaStream_t st);
+                  int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
+                  cudaStream_t st);
 
 // Separable form: 1-D spacings of a Cartesian-product grid from device
 // coordinates (FP64 derivative stencils of the metric computation).

@@ -32,7 +32,7 @@ EXPORTED = [
     "les_set_state_jet", "les_step", "les_get_state", "les_get_state_jet", "les_set_time",
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
-    "les_last_launch_count", "les_diag_sums_noalloc", "les_describe",
+    "les_set_fused_tiling", "les_last_launch_count", "les_diag_sums_noalloc", "les_describe",
     "les_last_error", "les_destroy",
 ]
 
@@ -93,6 +93,7 @@ def lib():
         L.les_debug_rhs.argtypes = [vp, ctypes.c_int, _dp]
         L.les_debug_field.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp]
         L.les_profile_step.argtypes = [vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]
+        L.les_set_fused_tiling.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.les_last_launch_count.argtypes = [vp]
         L.les_last_launch_count.restype = ctypes.c_int64
         L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
@@ -264,6 +265,11 @@ def les_profile_step(h, nsteps: int):
 
 def les_describe(h) -> str:
     return (lib().les_describe(h) or b"").decode()
+
+
+def les_set_fused_tiling(h, ty: int, kc: int):
+    """Fix the fused FP32 stage's tile height (8 or 16) and k-chunk (0 = balanced)."""
+    _check(h, lib().les_set_fused_tiling(h, int(ty), int(kc)))
 
 
 def les_last_launch_count(h) -> int:

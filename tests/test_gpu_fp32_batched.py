@@ -5,7 +5,8 @@
   scale, FP32 rounding of fluxes that are differences of O(1) terms);
 - batched jets (uneven grids, per-jet Mach/TR/Re/seed, one persistent launch
   per stage) are bit-identical to single-jet runs of the same precision;
-- the fused stage does not depend on its k-chunk or tile height.
+- the fused stage gives the same bits for every tile height and k-chunk,
+  and for the balanced tile-plane ranges (les_set_fused_tiling).
 """
 import numpy as np
 import pytest
@@ -124,3 +125,40 @@ def test_batched_fp32_against_oracle():
     b.close()
     print("batched fp32 jet 1, 20 steps, rel L2 per field:", err)
     assert np.all(err[[0, 1, 4]] <= 1e-5) and np.all(err <= 5e-5), err
+
+
+@pytest.mark.parametrize("prec", [les.LES_FP32, les.LES_FP32_SEPARABLE])
+def test_fused_stage_independent_of_tiling(prec):
+    """Every work decomposition of the fused stage (tile height 8 or 16; fixed
+    k-chunks, including a chunk of one plane; the balanced tile-plane ranges
+    whose cuts fall mid-column) gives the same bits, on a batch of uneven
+    jets."""
+    jets = I.batch_jets(4, seed=11)
+    specs = [g for g, _ in jets]
+    fps = [f for _, f in jets]
+    out = []
+    for ty, kc in ((8, 100000), (16, 100000), (8, 1), (16, 5), (8, 0), (16, 0)):
+        b = les.Solver(specs, fps, prec)
+        for j, (g, f) in enumerate(jets):
+            b.set_state(I.smooth_random_primitives(g, 40 + j, amp=0.05), jet=j)
+        les.les_set_fused_tiling(b.h, ty, kc)
+        b.step(3)
+        out.append([b.get_state(les.LES_STATE_RAW, jet=j) for j in range(len(jets))])
+        assert f"ty={ty}" in les.les_describe(b.h)
+        b.close()
+    for other in out[1:]:
+        for a, c in zip(out[0], other):
+            np.testing.assert_array_equal(a, c)
+
+
+def test_fused_tiling_arguments_checked():
+    spec, fp = I.jet_small()
+    s = les.Solver(spec, fp, les.LES_FP32)
+    for ty, kc in ((4, 0), (8, -1)):
+        with pytest.raises(les.LesError):
+            les.les_set_fused_tiling(s.h, ty, kc)
+    s.close()
+    s = les.Solver(spec, fp, les.LES_FP64)
+    with pytest.raises(les.LesError):
+        les.les_set_fused_tiling(s.h, 8, 0)
+    s.close()
