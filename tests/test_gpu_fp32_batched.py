@@ -162,3 +162,24 @@ def test_fused_tiling_arguments_checked():
     with pytest.raises(les.LesError):
         les.les_set_fused_tiling(s.h, 8, 0)
     s.close()
+
+
+@pytest.mark.slow
+def test_config4_batch64_bit_identical_to_single_jets():
+    """The 64-jet batch of the batched benchmark form (master seed 4), FP32,
+    one persistent launch per stage in a captured step: every jet's state after
+    3 steps has the same bits as the same jet run alone."""
+    jets = I.batch_jets(64, seed=4)
+    specs = [g for g, _ in jets]
+    fps = [f for _, f in jets]
+    b = les.Solver(specs, fps, les.LES_FP32)
+    for j, (g, f) in enumerate(jets):
+        b.set_state(I.ambient_primitives(g.N, f.TR), jet=j)
+    b.step(3)
+    for j, (g, f) in enumerate(jets):
+        s = les.Solver(g, f, les.LES_FP32)
+        s.set_state(I.ambient_primitives(g.N, f.TR))
+        s.step(3)
+        np.testing.assert_array_equal(b.get_state(les.LES_STATE_RAW, jet=j), s.get_state(les.LES_STATE_RAW))
+        s.close()
+    b.close()
