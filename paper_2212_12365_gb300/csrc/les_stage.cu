@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
             F[3 * fs] = rw * JU + p * mz;
             F[4 * fs] = rH * JU;
         }
-        const real s01 = sqrt(lam[0] * lam[1]), s02 = sqrt(lam[0] * lam[2]),
-                   s12 = sqrt(lam[1] * lam[2]);
+        // lambda_a + (lambda_a lambda_b)^1/2 + (lambda_a lambda_d)^1/2 = s_a (s_a + s_b + s_d)
+        const real sq0 = sqrt(lam[0]), sq1 = sqrt(lam[1]), sq2 = sqrt(lam[2]);
+        const real ssum = sq0 + sq1 + sq2;
         P[P_RHO * fs + lp] = rho;
         P[P_U * fs + lp] = u;
         P[P_V * fs + lp] = v;
@@ -101,9 +102,9 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
         P[P_T * fs + lp] = T;
         P[P_MU * fs + lp] = mu;
         // lambda-bar_a = lambda_a [1 + (lambda_b/lambda_a)^1/2 + (lambda_d/lambda_a)^1/2]
-        P[P_LXI * fs + lp] = lam[0] + s01 + s02;
-        P[P_LETA * fs + lp] = lam[1] + s01 + s12;
-        P[P_LZETA * fs + lp] = lam[2] + s02 + s12;
+        P[P_LXI * fs + lp] = sq0 * ssum;
+        P[P_LETA * fs + lp] = sq1 * ssum;
+        P[P_LZETA * fs + lp] = sq2 * ssum;
         P[P_RU * fs + lp] = ru;
         P[P_RV * fs + lp] = rv;
         P[P_RW * fs + lp] = rw;
