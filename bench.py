@@ -40,7 +40,7 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
                            "fp32-sep": 14 * 4}
 # DRAM bytes per point of one launch of the dominant kernel, from the ncu
 # captures summarised in profiles/ (None once the kernel changed since).
-TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 100.9}
+TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 100.4}
 # Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -272,6 +272,9 @@ def run_ours(args):
                         stream=les.ctypes.c_void_p(stream.cuda_stream))
     for j, (g, f) in enumerate(zip(specs, fps)):
         solver.set_state(I.ambient_primitives(g.N, f.TR), les.LES_STATE_PRIMITIVE, jet=j)
+    if args.tiling and P != les.LES_FP64:
+        ty, kc = (int(v) for v in args.tiling.split(","))
+        les.les_set_fused_tiling(solver.h, ty, kc)
     probe = None
     if args.probe or args.workload == "jet-768x384x192":
         # cylinder r = 3D, 256 azimuths x 384 axial stations, every 5 steps
@@ -369,6 +372,7 @@ def run_ours(args):
                            "mach_j": [f.mach_j for f in fps] if batch else fp.mach_j,
                            "TR": [round(f.TR, 3) for f in fps] if batch else fp.TR,
                            "Re_D": [round(f.Re) for f in fps] if batch else fp.Re,
+                           "tiling": args.tiling,
                            "probe": None if probe is None else {"points": int(probe.shape[2]), "every": 5,
                                                                  "frames": les.les_probe_frames(solver.h)},
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -396,6 +400,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 line of the FP64 default run")
     ap.add_argument("--probe", action="store_true", help="register the cylinder surface probe")
+    ap.add_argument("--tiling", default=None,
+                    help="TY,KC: fix the fused FP32 stage's tile height and k-chunk (0 = balanced) "
+                         "instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
