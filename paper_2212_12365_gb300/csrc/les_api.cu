@@ -526,6 +526,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             F.suth1 = (float)(1.0 + S);
             F.suthS = (float)S;
             F.cs2 = (float)(pp.Cs * pp.Cs);
+            F.pinf = (float)(1.0 / pp.gamma);
             for (int a = 0; a < 3; ++a) h->fj[j].h1[a] = h->J[j].h1[a];
             h->fj[j].mp = h->J[j].mp;
         }

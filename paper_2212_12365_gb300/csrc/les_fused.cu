@@ -178,9 +178,15 @@ __device__ __forceinline__ void fused_iface(const Sm<TY> &S, const FusedParams &
         const float JUL = L.m[3 * A] * L.a.y + L.m[3 * A + 1] * L.a.z + L.m[3 * A + 2] * L.a.w;
         const float JUR = mR[3 * A] * ra.y + mR[3 * A + 1] * ra.z + mR[3 * A + 2] * ra.w;
         H[0] = 0.5f * (LW[0] * JUL + WR[0] * JUR);
-        H[1] = 0.5f * (LW[1] * JUL + L.p * L.m[3 * A] + WR[1] * JUR + rb.x * mR[3 * A]);
-        H[2] = 0.5f * (LW[2] * JUL + L.p * L.m[3 * A + 1] + WR[2] * JUR + rb.x * mR[3 * A + 1]);
-        H[3] = 0.5f * (LW[3] * JUL + L.p * L.m[3 * A + 2] + WR[3] * JUR + rb.x * mR[3 * A + 2]);
+        // pressure terms with the ambient pressure taken out: a constant
+        // pressure has no flux divergence (metric identities), and leaving it
+        // in would add FP32 rounding of O(1) terms to the small transverse
+        // momentum residuals, and the metric identities' FP32 round-off
+        // times p_inf as a spurious source
+        const float pL = L.p - FP.pinf, pR = rb.x - FP.pinf;
+        H[1] = 0.5f * (LW[1] * JUL + pL * L.m[3 * A] + WR[1] * JUR + pR * mR[3 * A]);
+        H[2] = 0.5f * (LW[2] * JUL + pL * L.m[3 * A + 1] + WR[2] * JUR + pR * mR[3 * A + 1]);
+        H[3] = 0.5f * (LW[3] * JUL + pL * L.m[3 * A + 2] + WR[3] * JUR + pR * mR[3 * A + 2]);
         H[4] = 0.5f * (LW[4] * JUL + WR[4] * JUR);
     }
     // transport coefficients, sensor and lambda-bar at R
@@ -305,7 +311,7 @@ __device__ __forceinline__ void fused_iface_sep(const Sm<TY> &S, const FusedPara
         const float JUL = Sa * cmp(L.a, 1 + A), JUR = Sa * cmp(ra, 1 + A);
 #pragma unroll
         for (int f = 0; f < 5; ++f) H[f] = 0.5f * (LW[f] * JUL + WR[f] * JUR);
-        H[1 + A] += 0.5f * Sa * (L.p + rb.x);
+        H[1 + A] += 0.5f * Sa * ((L.p - FP.pinf) + (rb.x - FP.pinf)); // ambient pressure out, as above
     }
     float mueL, kapL, nuL, lbL, mueR, kapR, nuR, lbR;
     if (A == 0) {

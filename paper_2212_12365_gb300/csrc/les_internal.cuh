@@ -187,6 +187,7 @@ struct FusedParams {
     float inv_Re, kap_mol, kap_sgs;
     float suth1, suthS;     // Sutherland: mu = T^1.5 suth1 / (T + suthS)
     float cs2;              // Smagorinsky C_s^2 (separable form: (C_s Delta)^2 = cs2 (h_x h_y h_z)^(2/3))
+    float pinf;             // ambient pressure 1/gamma: subtracted from p in the pressure flux terms
 };
 
 // Work-list entry of one jet for the fused stage kernel: items
