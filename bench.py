@@ -44,6 +44,7 @@ TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 100.
 # Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
 def _batch64():
     jets = I.batch_jets(64, seed=4)
@@ -170,6 +171,21 @@ def cpu_baseline(spec, fp, budget_s=12.0, steps=1):
     return {"value": best[0], "unit": "grid-point-stage updates/s", "cores": cores, "kind": "oracle",
             "sample": f"{steps} RK step(s) on a {ni}x{nj}x{best[2]} k-slab of the workload "
                       f"({best[1]:.1f} s)"}
+
+
+def cpu_baseline_1core(workload, budget_s=4.0):
+    """The same oracle sample on one host core (OpenMP limited to one thread in
+    a child process; it touches no GPU)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "spec, fp = bench.WORKLOADS[%r][0](); "
+            "print(json.dumps(bench.cpu_baseline(spec, fp, budget_s=%r)))" % (ROOT, workload, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=300, check=True).stdout
+        return json.loads(out.strip().splitlines()[-1])
+    except Exception:
+        return None
 
 
 def run_reference(args):
@@ -330,7 +346,10 @@ def run_ours(args):
                 "hbm_view": {"algorithmic_bytes_per_point_stage": bytes_pt_stage,
                              "achieved_gbs": value * bytes_pt_stage / 1e9 / ws,
                              "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)",
-                             "frac": value * bytes_pt_stage / 1e9 / ws / hbm_peak}}
+                             "frac": value * bytes_pt_stage / 1e9 / ws / hbm_peak,
+                             "frac_nominal": value * bytes_pt_stage / 1e9 / ws / HBM_NOMINAL_GBS,
+                             # DRAM bytes of the dominant kernel (ncu capture) over its event-timed launch
+                             "dominant_kernel_dram_gbs": traffic_pt * N / t_launch / 1e9 if traffic_pt else None}}
 
     # end to end through the public API: pinned host state in, step, state out
     e2e = None
@@ -356,6 +375,10 @@ def run_ours(args):
     # (a k-slab of a polar mesh would cut its azimuthal period: no CPU sample there)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not batch and not spec.periodic[2]:
         cpu = cpu_baseline(spec, fp)
+        one = cpu_baseline_1core(args.workload)
+        if one:
+            cpu["value_1core"] = one["value"]
+            cpu["sample_1core"] = one["sample"] + ", 1 thread"
     secondary = None
     if rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64" and not args.no_fp32:
         secondary = precision_form(args, spec, fp, les, torch, value)
