@@ -5,7 +5,8 @@
   restarted from the GPU state at step 990 (the oracle cannot march 1000
   steps of 14M points in test time, but it can march the last 10).
 - The same jet in FP32: per-field relative L2 against the FP64 GPU path
-  after 100 and 1000 steps (reported; bounded).
+  after 100 and 1000 steps (reported; bounded), and after 1000 steps also
+  over the interior away from the boundary planes.
 - Large FP32 jet, 768x384x192, TR 2, 500 steps with the surface probe on a
   cylinder r = 3 every 5 steps: the state stays finite and the probe ring
   holds the expected frames, the last of which matches the oracle's
@@ -97,10 +98,18 @@ def test_paper_scale_fp32_error_100_and_1000_steps(fp64_run):
     q = s.get_state(les.LES_STATE_CONSERVED)
     s.close()
     e1000 = rel_l2(q, out["q1000"])
-    print("fp32 vs fp64 rel L2 per field, 100 steps:", e100, " 1000 steps:", e1000)
+    # the interior (8-point margin) without the boundary planes, where the
+    # far-field condition of the inflow face may take the other branch in
+    # FP32 for a normal velocity near zero
+    ni, nj, nk = spec.dims
+    d = (q - out["q1000"]).reshape(5, nk, nj, ni)[:, 8:-8, 8:-8, 8:-8]
+    den = np.sqrt((out["q1000"] ** 2).sum(axis=1))
+    ein = np.sqrt((d.reshape(5, -1) ** 2).sum(axis=1)) / den
+    print("fp32 vs fp64 rel L2 per field, 100 steps:", e100, " 1000 steps:", e1000, " interior:", ein)
     assert np.all(np.isfinite(q))
     assert np.all(e100[[0, 1, 4]] <= 1e-5) and np.all(e100 <= 5e-5), e100
     assert np.all(e1000 <= 1e-3), e1000
+    assert np.all(ein[[0, 1, 4]] <= 1e-5) and np.all(ein <= 2e-5), ein
 
 
 def test_large_fp32_500_steps_with_probe():
