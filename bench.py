@@ -140,6 +140,24 @@ def dist_env():
     return ws, rank, local
 
 
+def host_cpu():
+    """Host CPU description: architecture and model (x86 'model name', or the
+    Arm implementer/part numbers)."""
+    import platform
+    model = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        kv = [l.split(":", 1) for l in info if ":" in l]
+        d = {}
+        for k, v in kv:
+            d.setdefault(k.strip(), v.strip())
+        model = d.get("model name") or (f"implementer {d.get('CPU implementer')} part {d.get('CPU part')}"
+                                        if "CPU part" in d else None)
+    except OSError:
+        pass
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(spec, fp, budget_s=12.0, steps=1):
     """The oracle as it stands on a bounded k-slab of the workload: one RK step
     (5 stages); the slab grows until the run takes ~budget_s."""
@@ -170,7 +188,7 @@ def cpu_baseline(spec, fp, budget_s=12.0, steps=1):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": best[0], "unit": "grid-point-stage updates/s", "cores": cores, "kind": "oracle",
             "sample": f"{steps} RK step(s) on a {ni}x{nj}x{best[2]} k-slab of the workload "
-                      f"({best[1]:.1f} s)"}
+                      f"({best[1]:.1f} s)", "cpu": host_cpu()}
 
 
 def cpu_baseline_1core(workload, budget_s=4.0):
@@ -188,13 +206,32 @@ def cpu_baseline_1core(workload, budget_s=4.0):
         return None
 
 
+def workload_config(args, prec, specs, fps, batch, ws, probe=None):
+    """The JSON line's config object (the same for both arms of a workload)."""
+    return {"workload": args.workload, "precision": prec, "points": sum(g.N for g in specs),
+            "grid": [list(g.dims) for g in specs] if batch else list(specs[0].dims),
+            "jets": len(specs),
+            "mach_j": [f.mach_j for f in fps] if batch else fps[0].mach_j,
+            "TR": [round(f.TR, 3) for f in fps] if batch else fps[0].TR,
+            "Re_D": [round(f.Re) for f in fps] if batch else fps[0].Re,
+            "tiling": args.tiling,
+            "probe": probe,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2 (state + metrics + scratch are GBs)"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    make, prec = WORKLOADS[args.workload]
+    make, prec_default = WORKLOADS[args.workload]
+    prec = args.precision or prec_default
     spec, fp = make()
-    if isinstance(spec, list):  # a batch: the oracle samples its first jet
+    batch = isinstance(spec, list)
+    cfg = workload_config(args, prec, spec if batch else [spec], fp if batch else [fp], batch, ws,
+                          None if not (args.probe or args.workload == "jet-768x384x192") else
+                          {"points": 256 * 384, "every": 5, "frames": None})
+    if batch:  # a batch: the oracle samples its first jet
         spec, fp = spec[0], fp[0]
     import oracle  # noqa: F401
     oracle.build()
@@ -211,7 +248,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "precision": "fp64", "points": spec.N},
+            "config": cfg,
             "cpu_baseline": {**vals[0], "value": v},
             "e2e": {"value": v, "unit": "grid-point-stage updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -309,15 +346,19 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one event per step boundary (the steps run back to back; the events
+    # only give the per-step spread)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
     with ClockSampler(local) as clk:
-        ev0.record(stream)
-        solver.step(args.steps)
-        ev1.record(stream)
+        evs[0].record(stream)
+        for i in range(args.steps):
+            solver.step(1)
+            evs[i + 1].record(stream)
         barrier()
-    launches = les.les_last_launch_count(solver.h)
-    value, ms = aggregate_rate(ev0.elapsed_time(ev1), N, args.steps, ws, "cuda")
+    launches = les.les_last_launch_count(solver.h) * args.steps
+    value, ms = aggregate_rate(evs[0].elapsed_time(evs[-1]), N, args.steps, ws, "cuda")
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
 
     # per-kernel device time of the same stage sequence, eager with events
     prof = les.les_profile_step(solver.h, max(1, min(args.steps, 3)))
@@ -386,20 +427,15 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": "grid-point-stage updates/s", "value": value,
                 "unit": "grid-point-stage updates/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "step_ms": {"best": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
+                "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "precision": prec, "points": N,
-                           "grid": [list(g.dims) for g in specs] if batch else list(spec.dims),
-                           "jets": len(specs),
-                           "mach_j": [f.mach_j for f in fps] if batch else fp.mach_j,
-                           "TR": [round(f.TR, 3) for f in fps] if batch else fp.TR,
-                           "Re_D": [round(f.Re) for f in fps] if batch else fp.Re,
-                           "tiling": args.tiling,
-                           "probe": None if probe is None else {"points": int(probe.shape[2]), "every": 5,
-                                                                 "frames": les.les_probe_frames(solver.h)},
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "l2": "inputs larger than L2 (state + metrics + scratch are GBs)"},
+                "config": workload_config(args, prec, specs, fps, batch, ws,
+                                          None if probe is None else
+                                          {"points": int(probe.shape[2]), "every": 5,
+                                           "frames": les.les_probe_frames(solver.h)}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "precision_form": secondary,
                 "clocks": clk.summary()}
