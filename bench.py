@@ -399,6 +399,7 @@ def run_ours(args):
         host_out = torch.empty((5, N), dtype=torch.float64, pin_memory=True)
         host_in.numpy()[:] = solver.get_state(les.LES_STATE_RAW)
         ke = max(2, min(args.steps, 5))
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         torch.cuda.synchronize()
         ev0.record(stream)
