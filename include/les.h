@@ -13,9 +13,11 @@
  * - Grids are structured with ni x nj x nk points; host arrays are dense,
  *   point (i,j,k) at linear index (k*nj + j)*ni + i (i = xi = axial fastest).
  *   Field arrays of 5 variables are [field][point] (5*N doubles).
- * - The stored state is Qhat = J^-1 [rho, rho u, rho v, rho w, e]
- *   (Eq. hat_Q_vec); the API exchanges the unscaled Q, primitives
- *   (rho, u, v, w, p), or the raw stored Qhat.
+ * - The scheme advances Qhat = J^-1 [rho, rho u, rho v, rho w, e]
+ *   (Eq. hat_Q_vec).  FP64 handles store Qhat; FP32 handles store the
+ *   unscaled Q and advance it by the same update times J (a uniform flow is
+ *   then stored exactly alike at every point).  The API exchanges the
+ *   unscaled Q, primitives (rho, u, v, w, p), or the raw stored state.
  * - Every function returns LES_OK (0) or a negative LES_ERR_* code; the text
  *   of the last error of a handle is returned by les_last_error().  A
  *   NULL handle or pointer where one is required gives LES_ERR_ARG.  CUDA
@@ -76,7 +78,8 @@ extern "C" {
 /* State kinds for les_set_state / les_get_state. */
 #define LES_STATE_CONSERVED 0 /* unscaled Q = [rho, rho u, rho v, rho w, e] */
 #define LES_STATE_PRIMITIVE 1 /* [rho, u, v, w, p] */
-#define LES_STATE_RAW 2       /* stored Qhat = J^-1 Q, for bit-exact checkpoints */
+#define LES_STATE_RAW 2       /* the stored state, for bit-exact checkpoints: Qhat = J^-1 Q
+                                 (FP64 handles) or Q (FP32 handles) */
 
 /* Point fields for les_debug_field. */
 #define LES_FIELD_MU_SGS 0   /* Smagorinsky mu_sgs (Sec. "Subgrid Scale Viscosity") */
@@ -239,7 +242,8 @@ int64_t les_last_launch_count(les_handle *h);
  * synchronisation.  It computes what les_get_diagnostics reports from the
  * caller's own buffers:
  *   qhat, rhs : device arrays of 5*npoints doubles, [field][point] (dense
- *               layout of les_get_state LES_STATE_RAW and les_debug_rhs);
+ *               layout of les_get_state and les_debug_rhs; qhat = J^-1 Q,
+ *               the raw state of an FP64 handle);
  *               rhs should be zero at boundary points;
  *   out       : device array of 12 doubles: [0] max |rhs_rho|,
  *               [1..5] sqrt(sum rhs_f^2), [6..10] compensated sum of qhat_f,

@@ -473,7 +473,6 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         const long long fs = J.fs;
         const long long plane = (long long)nj * J.pitch;
         const float *__restrict__ Qs = J.q[src];
-        const float *__restrict__ M = J.met;
         float *__restrict__ Qd = J.q[dst];
         const float adt = rhs_only ? 0.0f : c_alpha_f[stage] * (float)dt[jet];
 
@@ -526,14 +525,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
         for (int t = 0; t < 6; ++t) sl[t] = ring5(k0 - 4 - 5 + t);
 
+        // J of this thread's column at the plane of the next update (the
+        // state is stored unscaled, so the update is Q(l) = Q(0) - alpha dt J R)
+        float rjU = 0.0f;
         __syncthreads(); // shared memory of the previous item is free
-        // separable form: J = 1/(hx hy hz) of the load-phase cells, in-plane part
-        float rJ2[2] = {0.0f, 0.0f};
-        if constexpr (SEP) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-                if (lc[t] >= 0) rJ2[t] = S.HX[lc[t] % C2X].y * S.HY[lc[t] / C2X].y;
-        }
         // separable form: the state of plane kq (this thread's load cells) and
         // Q(0) of its output column at plane ku are staged in shared memory
         // one iteration ahead by asynchronous copies, so the load phase and the
@@ -590,16 +585,13 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 nrm[2] = a3.z;
             }
             const int gkL = gidx(kL, nk, pk);
-            float qv[2][5], rjc[2];
+            float qv[2][5];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                rjc[t] = 0.0f;
+            for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) qv[t][f] = 0.0f;
-            }
             if constexpr (SEP) cp_async_wait_all();
             if (gkL >= 0) {
-                const float rhzL = SEP ? F.h1[2][gkL].y : 0.0f;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
@@ -607,11 +599,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     if constexpr (SEP) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
-                        rjc[t] = rJ2[t] * rhzL;
                     } else {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
-                        rjc[t] = M[MET_J * fs + o];
                     }
                 }
             }
@@ -625,12 +615,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
-                    const float rj = rjc[t];
-                    const float rho = qv[t][0] * rj;
+                    const float rho = qv[t][0];
                     const float rr = 1.0f / rho;
-                    const float rrj = rj * rr;
-                    const float u = qv[t][1] * rrj, v = qv[t][2] * rrj, w = qv[t][3] * rrj;
-                    const float e = qv[t][4] * rj;
+                    const float u = qv[t][1] * rr, v = qv[t][2] * rr, w = qv[t][3] * rr;
+                    const float e = qv[t][4];
                     const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
                     S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
                     S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
@@ -840,11 +828,19 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                             for (int f = 0; f < 5; ++f) q0v[f] = q0s[f];
                         }
+                        float rjk;
+                        if constexpr (SEP) {
+                            rjk = S.HX[tx + 1].y * S.HY[ty + 1].y * F.h1[2][gk].y;
+                        } else {
+                            rjk = rjU;
+                        }
+                        const float adtj = adt * rjk;
 #pragma unroll
-                        for (int f = 0; f < 5; ++f) Qd[f * fs + o] = q0v[f] - adt * R[f];
+                        for (int f = 0; f < 5; ++f) Qd[f * fs + o] = q0v[f] - adtj * R[f];
                     }
                 }
             }
+            if constexpr (!SEP) rjU = rjG; // plane kG is the next iteration's kU
             __syncthreads();
         }
     }

@@ -70,7 +70,7 @@ struct JetDev {
     // q[1], q[2] ping-pong stage registers
     real *q[3];
     const real *met;   // NMET fields
-    const double *jinv64; // J^-1 in FP64 (conversions of the state)
+    const double *jinv64; // J^-1 in FP64 (conversions of the state, Qhat sums)
     real *prim;        // NPRIM fields (scratch, rebuilt every stage)
     real *grad;        // NGRAD fields (scratch)
     real *hflux;       // NHF fields (scratch): interface fluxes
@@ -114,6 +114,19 @@ __host__ __device__ __forceinline__ long long lidx(const JetDev<real> &J, int i,
 // degenerate axis of a polar mesh (centerline face), where J^-1 = 0 and the
 // state is kept unscaled (Sec. "Centerline Boundary Condition").
 __host__ __device__ __forceinline__ double state_scale(double jinv) { return jinv > 0.0 ? jinv : 1.0; }
+
+// Scale of the state as stored by a handle of storage type `real`.  FP64
+// handles store Qhat = J^-1 Q, the variable the Runge-Kutta scheme advances.
+// FP32 handles store the unscaled Q and advance it as Q(l) = Q(0) - alpha_l
+// dt J RHS, the same update multiplied by J: a uniform state is then stored
+// exactly alike at every point, whereas FP32 rounding of J^-1 Q on a
+// stretched grid seeds a point-to-point pressure noise that drives the
+// transverse momenta.
+template <typename real> __host__ __device__ __forceinline__ double stored_scale(double jinv)
+{
+    if constexpr (sizeof(real) == sizeof(float)) return 1.0;
+    else return state_scale(jinv);
+}
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n)
 {

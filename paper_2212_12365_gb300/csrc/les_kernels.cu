@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(BLOCK) k_centerline(const JetDev<real> *__rest
     double sum = 0.0;
     for (int k = 0; k < J.n[2]; ++k) {
         const long long o = lidx(J, i, 1, k);
-        sum += (double)Q[o] / state_scale(J.jinv64[o]);
+        sum += (double)Q[o] / stored_scale<real>(J.jinv64[o]);
     }
     const double avg = sum / (double)J.n[2];
     for (int k = 0; k < J.n[2]; ++k) Q[lidx(J, i, 0, k)] = (real)avg;
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         }
         const T rn = rsqrt(nn);
         for (int c = 0; c < 3; ++c) n[c] *= rn;
-        const T jinvE = (T)state_scale(J.jinv64[E]), jinvF = (T)state_scale(J.jinv64[F]);
+        const T jinvE = (T)stored_scale<real>(J.jinv64[E]), jinvF = (T)stored_scale<real>(J.jinv64[F]);
         const T rjE = T(1) / jinvE;
         T Qe[5], Qf[5];
         for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] * rjE;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(BLOCK) k_set_state(const JetDev<real> *__restr
         } else {
             for (int f = 0; f < 5; ++f) Qc[f] = v[f];
         }
-        const double jinv = state_scale(J.jinv64[lp]);
+        const double jinv = stored_scale<real>(J.jinv64[lp]);
         for (int f = 0; f < 5; ++f) Q[f * J.fs + lp] = (real)(jinv * Qc[f]);
     }
 }
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(BLOCK) k_get_state(const JetDev<real> *__restr
         double v[5];
         for (int f = 0; f < 5; ++f) v[f] = (double)Q[f * J.fs + lp];
         if (kind != LES_STATE_RAW) {
-            const double jinv = state_scale(J.jinv64[lp]);
+            const double jinv = stored_scale<real>(J.jinv64[lp]);
             for (int f = 0; f < 5; ++f) v[f] /= jinv;
             if (kind == LES_STATE_PRIMITIVE) {
                 Prim64 s = prim_of(v, J.gamma);
@@ -615,9 +615,12 @@ __global__ void __launch_bounds__(BLOCK) k_diag_partials(const JetDev<real> *__r
          lp += (long long)gridDim.x * blockDim.x) {
         int q[3];
         if (!point_of(J, lp, q)) continue;
+        // the Qhat the FP64 store holds (unscaled on a polar axis) from an
+        // unscaled FP32 store
+        const double qs = sizeof(real) == sizeof(float) ? state_scale(J.jinv64[lp]) : 1.0;
         for (int f = 0; f < 5; ++f) {
             double r = (double)J.rhs[f * fs + lp];
-            double v = (double)J.q[0][f * fs + lp];
+            double v = (double)J.q[0][f * fs + lp] * qs;
             if (!isfinite(r) || !isfinite(v)) bad += 1.0;
             l2[f] += r * r;
             neumaier_add(s[f], c[f], v);
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(BLOCK) k_probe(const JetDev<real> *__restrict_
                 wgt *= up ? t[a] : 1.0 - t[a];
             }
             long long p = lidx(J, r[0], r[1], r[2]);
-            double jinv = state_scale(J.jinv64[p]);
+            double jinv = stored_scale<real>(J.jinv64[p]);
             double Q[5];
             for (int f = 0; f < 5; ++f) Q[f] = (double)J.q[0][f * fs + p] / jinv;
             Prim64 pr = prim_of(Q, g);

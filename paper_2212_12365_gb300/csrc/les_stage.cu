@@ -66,9 +66,12 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
         real *__restrict__ P = J.prim;
         const real gam = (real)J.gamma;
         const real rj = M[MET_J * fs + lp];
-        const real rho = Q[lp] * rj;
-        const real ru = Q[fs + lp] * rj, rv = Q[2 * fs + lp] * rj, rw = Q[3 * fs + lp] * rj;
-        const real e = Q[4 * fs + lp] * rj;
+        // the stored state times rq is Q: J for a Qhat store, 1 for an
+        // unscaled FP32 store
+        const real rq = sizeof(real) == sizeof(float) ? real(1) : rj;
+        const real rho = Q[lp] * rq;
+        const real ru = Q[fs + lp] * rq, rv = Q[2 * fs + lp] * rq, rw = Q[3 * fs + lp] * rq;
+        const real e = Q[4 * fs + lp] * rq;
         const real rrho = rcp_<real>(rho);
         const real u = ru * rrho, v = rv * rrho, w = rw * rrho;
         const real p = (gam - real(1)) * (e - real(0.5) * (ru * u + rv * v + rw * w));

@@ -183,3 +183,45 @@ def test_config4_batch64_bit_identical_to_single_jets():
         np.testing.assert_array_equal(b.get_state(les.LES_STATE_RAW, jet=j), s.get_state(les.LES_STATE_RAW))
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", [les.LES_FP32, les.LES_FP32_SEPARABLE])
+def test_fp32_unscaled_store_state_and_diagnostics(prec):
+    """FP32 handles store the unscaled Q: a uniform ambient state is stored
+    bit-identically at every point of a stretched grid and stays so over a
+    step (the far-field faces see the ambient itself); the raw state is Q; the
+    conservation sums are those of Qhat = J^-1 Q (FP64, against the oracle's
+    sums of the same state)."""
+    spec, fp = I.jet_small()
+    ni, nj, nk = spec.dims
+    s = les.Solver(spec, fp, prec)
+    amb = I.ambient_primitives(spec.N, fp.TR)
+    s.set_state(amb, les.LES_STATE_PRIMITIVE)
+    raw = s.get_state(les.LES_STATE_RAW)
+    q = s.get_state(les.LES_STATE_CONSERVED)
+    np.testing.assert_array_equal(raw, q)
+    # every interior point holds the same FP32 words
+    body = raw.reshape(5, nk, nj, ni)[:, 1:-1, 1:-1, 1:-1]
+    for f in range(5):
+        assert np.unique(body[f]).size == 1, f
+    ref = body[:, 0, 0, 0].copy()
+    s.step(1)
+    q1 = s.get_state(les.LES_STATE_CONSERVED).reshape(5, nk, nj, ni)
+    # points no face reaches within one step (5 stages x 2 points) keep the
+    # ambient to far below FP32 rounding (a J^-1-scaled FP32 store gives
+    # differences of ~1e-8 here)
+    far = q1[:, 11:nk - 11, 11:nj - 11, ni // 2:ni - 11]
+    dev = np.abs(far - ref[:, None, None, None]).max(axis=(1, 2, 3))
+    assert np.all(dev <= 1e-12), dev
+    # conservation sums: Qhat of the (FP32-valued) state, summed in FP64
+    s.set_state(I.smooth_random_primitives(spec, seed=31, amp=0.05), les.LES_STATE_PRIMITIVE)
+    s.step(2)
+    qc = s.get_state(les.LES_STATE_CONSERVED)
+    d = s.diagnostics()
+    s.close()
+    g, p = to_oracle(spec, fp)
+    m = oracle.metrics(g)
+    dor = oracle.diag(g, p, m, oracle.qhat_from(g, p, m, qc, False))
+    qh = oracle.qhat_from(g, p, m, qc, False)
+    mag = np.abs(qh).sum(axis=1)
+    assert np.all(np.abs(d["sum_qhat"] - dor["sum_qhat"]) <= 1e-13 * mag), (d["sum_qhat"], dor["sum_qhat"])

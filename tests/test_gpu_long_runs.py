@@ -126,7 +126,6 @@ def test_large_fp32_500_steps_with_probe():
     torch.cuda.synchronize()
     nfr = les.les_probe_frames(s.h)
     q = s.get_state(les.LES_STATE_CONSERVED)
-    raw = s.get_state(les.LES_STATE_RAW)
     d = s.diagnostics()
     s.close()
     assert nfr == 100
@@ -136,7 +135,7 @@ def test_large_fp32_500_steps_with_probe():
     # the last frame (step 500) against the oracle's probe of the final state
     g, p = to_oracle(spec, fp)
     m = oracle.metrics(g)
-    ref = oracle.probe(g, p, m, raw.astype(np.float64), xyz)
+    ref = oracle.probe(g, p, m, oracle.qhat_from(g, p, m, q, False), xyz)
     last = frames[(nfr - 1) % cap]
     scale = np.abs(ref).max(axis=1, keepdims=True)
     err = np.abs(last - ref) / scale
