@@ -225,7 +225,7 @@ __device__ __forceinline__ void fused_iface(const Sm<TY> &S, const FusedParams &
     }
     // compact viscous + SGS flux
     {
-        const float rjb = 1.0f / jb;
+        const float rjb = __fdividef(1.0f, jb);
         constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2; // tangential axes
         const float4 dR1 = S.GD[(rpl * 3 + B1) * N1 + r1], dR2 = S.GD[(rpl * 3 + B2) * N1 + r1];
         const float4 dL1 = S.GD[(L.pl * 3 + B1) * N1 + L.c1], dL2 = S.GD[(L.pl * 3 + B2) * N1 + L.c1];
@@ -343,7 +343,7 @@ __device__ __forceinline__ void fused_iface_sep(const Sm<TY> &S, const FusedPara
     }
     // compact viscous + SGS flux: only row A of the stress tensor is needed
     {
-        const float rhb = 1.0f / hb;
+        const float rhb = __fdividef(1.0f, hb);
         constexpr int B1 = A == 0 ? 1 : 0, B2 = A == 2 ? 1 : 2;
         const float4 dR1 = S.GD[(rpl * 3 + B1) * N1 + r1], dR2 = S.GD[(rpl * 3 + B2) * N1 + r1];
         const float4 dL1 = S.GD[(L.pl * 3 + B1) * N1 + L.c1], dL2 = S.GD[(L.pl * 3 + B2) * N1 + L.c1];
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
                     const float rho = qv[t][0];
-                    const float rr = 1.0f / rho;
+                    const float rr = __fdividef(1.0f, rho);
                     const float u = qv[t][1] * rr, v = qv[t][2] * rr, w = qv[t][3] * rr;
                     const float e = qv[t][4];
                     const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     }
                 }
                 const float rho = A0.x, T = B0.y;
-                const float mus = rho * csd2 * sqrtf(2.0f * ss);
+                const float mus = rho * csd2 * sqrt_nonneg(2.0f * ss);
                 const float sT = sqrt_pos(T);
                 const float mu = __fdividef(T * sT * FP.suth1, T + FP.suthS);
                 float lam[3];
