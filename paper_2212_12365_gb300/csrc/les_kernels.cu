@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         int jet = find_jet(bm, vb);
         const JetDev<real> &J = jets[jet];
         if (J.per[axis]) continue;
-        const int b = (axis + 1) % 3, d = (axis + 2) % 3;
+        // tangential axes, the lower one fastest across threads (i on the y
+        // and z faces, so those passes read and write whole rows)
+        const int b = axis == 0 ? 1 : 0, d = axis == 2 ? 1 : 2;
         const long long nface = (long long)J.n[b] * J.n[d];
         long long t = (long long)(vb - bm.start[jet]) * BLOCK + threadIdx.x;
         if (t >= 2 * nface) continue;
