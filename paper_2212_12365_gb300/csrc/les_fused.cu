@@ -93,7 +93,12 @@ __device__ __forceinline__ int ring2(int k) { return k & 1; } // two's complemen
 // Wrap a global index on a periodic axis; -1 for outside a non-periodic axis.
 __device__ __forceinline__ int gidx(int g, int n, int per)
 {
-    if (per) return wrapi(g, n);
+    if (per) {
+        // the tile and plane indices stray at most one period: a compare and
+        // an add, with the modulo only as a fallback
+        const int h = g < 0 ? g + n : (g >= n ? g - n : g);
+        return (unsigned)h < (unsigned)n ? h : wrapi(g, n);
+    }
     return (g >= 0 && g < n) ? g : -1;
 }
 
