@@ -61,11 +61,10 @@ template <int TY> struct Geo {
     static constexpr size_t O_MB = O_MA + 16ull * 2 * 2 * NC1;
     static constexpr size_t O_PB = O_MB + 8ull * 2 * NC1;
     static constexpr size_t O_SH = O_PB + 8ull * 5 * NC2;
-    // separable form: MA/MB hold no metrics; their 20 NT floats stage the
-    // state of the next plane and Q(0) (cp.async), see k_fused
-    static constexpr size_t O_QS = O_MA;                 // float [2 cells][5][NT]
-    static constexpr size_t O_Q0S = O_QS + 4ull * 10 * NT; // float [2 planes][5][NT]
-    static_assert(O_Q0S + 4ull * 10 * NT <= O_PB, "staging fits in MA+MB");
+    // separable form: MA/MB hold no metrics; 10 NT floats of them stage the
+    // state of the next plane (cp.async), see k_fused
+    static constexpr size_t O_QS = O_MA; // float [2 cells][5][NT]
+    static_assert(O_QS + 4ull * 10 * NT <= O_PB, "staging fits in MA+MB");
     static constexpr size_t O_HX = O_SH + 4ull * 5 * TY * FX;
     static constexpr size_t O_HY = O_HX + 16ull * C2X;
     static constexpr size_t BYTES = O_HY + 16ull * C2Y;
@@ -76,13 +75,13 @@ template <int TY> struct Sm {
     float2 *PB, *MB;
     float *SH;
     float4 *HX, *HY;
-    float *QS, *Q0S;
+    float *QS;
     __device__ __forceinline__ explicit Sm(unsigned char *b)
         : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
           GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
           PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH)),
           HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY)),
-          QS((float *)(b + Geo<TY>::O_QS)), Q0S((float *)(b + Geo<TY>::O_Q0S))
+          QS((float *)(b + Geo<TY>::O_QS))
     {
     }
 };
@@ -534,10 +533,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         // state is stored unscaled, so the update is Q(l) = Q(0) - alpha dt J R)
         float rjU = 0.0f;
         __syncthreads(); // shared memory of the previous item is free
-        // separable form: the state of plane kq (this thread's load cells) and
-        // Q(0) of its output column at plane ku are staged in shared memory
-        // one iteration ahead by asynchronous copies, so the load phase and the
-        // update find them there; each thread reads only what it copied
+        // separable form: the state of plane kq at this thread's load cells is
+        // staged in shared memory one iteration ahead by asynchronous copies,
+        // so the load phase finds it there; each thread reads only what it
+        // copied
         auto stage_q = [&](int kq) {
             const int gk = gidx(kq, nk, pk);
             if (kq > k1 + 2 || gk < 0) return;
@@ -548,14 +547,6 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) cp_async4(&S.QS[(t * 5 + f) * G_::NT + tid], Qs + f * fs + o);
             }
-        };
-        auto stage_q0 = [&](int ku) {
-            const int gk = gidx(ku, nk, pk);
-            if (rhs_only || !out_col || ku < k0 || ku >= k1 || gk < 0) return;
-            const long long o = gk * plane + ocol;
-            const float *Q0g = J.q[0];
-#pragma unroll
-            for (int f = 0; f < 5; ++f) cp_async4(&S.Q0S[(ring2(ku) * 5 + f) * G_::NT + tid], Q0g + f * fs + o);
         };
         if constexpr (SEP) {
             stage_q(k0 - 3);
@@ -851,8 +842,6 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     }
 }
 
-template <int TY> size_t fused_smem_bytes() { return Geo<TY>::BYTES; }
-
 template <int TY> int fused_prepare()
 {
     int rc = (int)cudaFuncSetAttribute(k_fused<TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -875,8 +864,6 @@ void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int 
                                                                rhs_only, balanced);
 }
 
-template size_t fused_smem_bytes<16>();
-template size_t fused_smem_bytes<8>();
 template int fused_prepare<16>();
 template int fused_prepare<8>();
 template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,

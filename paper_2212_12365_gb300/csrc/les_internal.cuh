@@ -220,7 +220,6 @@ struct FusedJet {
     const float4 *mp;
 };
 
-template <int TY> size_t fused_smem_bytes();
 template <int TY> int fused_prepare();
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
