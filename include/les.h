@@ -234,6 +234,23 @@ int les_set_fused_tiling(les_handle *h, int ty, int kc);
 /* Kernel launches issued by the most recent les_step call (all steps). */
 int64_t les_last_launch_count(les_handle *h);
 
+/* Index-bounds checking, the debug build that stands in for a memory
+ * checker.  A library compiled with -DLES_BOUNDS_CHECK checks, in every
+ * kernel, each point index against its grid (i, j, k within the axes) and,
+ * in the fused FP32 stage, every global offset against the padded point
+ * count and every shared-memory slot against its table; the first index out
+ * of range is recorded and that access is redirected to index 0 instead of
+ * faulting.  Results are otherwise those of the normal build.
+ * les_bounds_checking() returns 1 for such a library, 0 for a normal one.
+ * les_bounds_violation(h, out) writes the first violation of the kernels run
+ * for handle h since its creation: 0 if none, else (site << 48) | value with
+ * site 1 a point index (value = k << 32 | j << 16 | i, 16 bits each), 2-4 a
+ * fused-stage global offset (state, static record, update), 5-7 a fused-stage
+ * shared-memory slot (point ring, plane tables, eta-flux rows); always 0 in a
+ * normal build.  Synchronises the stream.  Errors: LES_ERR_ARG. */
+int les_bounds_checking(void);
+int les_bounds_violation(les_handle *h, uint64_t *out);
+
 /* Residual / conservation sums without any device allocation.  The paper
  * has no counterpart: this is a library service for callers that must not
  * allocate device memory — code inside a framework whose caching allocator

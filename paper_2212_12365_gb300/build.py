@@ -26,30 +26,34 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+BOUNDS_BUILD = os.path.join(HERE, "_build_bounds")
+BOUNDS_LIB = os.path.join(BOUNDS_BUILD, "libles.so")
+
+
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "les.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def _compile(build_dir: str, lib: str, extra: list[str]) -> list:
+    """Start the nvcc processes of one library; returns (src, process, obj)."""
+    os.makedirs(build_dir, exist_ok=True)
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH,
-             "-I", os.path.join(ROOT, "include"), "-I", CSRC] + (extra or [])
-    procs, objs = [], []
+             "-I", os.path.join(ROOT, "include"), "-I", CSRC] + extra
+    procs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(obj)
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), obj))
+    return procs
+
+
+def _link(lib: str, procs: list, verbose: bool) -> None:
     failed = []
-    for src, p in procs:
+    for src, p, _ in procs:
         out, _ = p.communicate()
         if p.returncode != 0:
             failed.append((src, out.decode(errors="replace")))
@@ -57,10 +61,32 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             print(out.decode(errors="replace"), file=sys.stderr)
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(f"[{s}]\n{o}" for s, o in failed))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *[o for _, _, o in procs], "-cudart", "static"],
+                   check=True)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          bounds: bool = False) -> str:
+    """libles.so (bounds=False) or its index-bounds-checked debug build
+    (-DLES_BOUNDS_CHECK, _build_bounds/libles.so); returns the library path."""
+    build_dir, lib = (BOUNDS_BUILD, BOUNDS_LIB) if bounds else (BUILD, LIB)
+    if not force and not _stale(lib):
+        return lib
+    _link(lib, _compile(build_dir, lib, (["-DLES_BOUNDS_CHECK"] if bounds else []) + (extra or [])), verbose)
+    return lib
+
+
+def build_all(force: bool = False, verbose: bool = False) -> tuple[str, str]:
+    """Both libraries, compiled in parallel."""
+    jobs = []
+    for bounds, (build_dir, lib) in ((False, (BUILD, LIB)), (True, (BOUNDS_BUILD, BOUNDS_LIB))):
+        if force or _stale(lib):
+            jobs.append((lib, _compile(build_dir, lib, ["-DLES_BOUNDS_CHECK"] if bounds else [])))
+    for lib, procs in jobs:
+        _link(lib, procs, verbose)
+    return LIB, BOUNDS_LIB
 
 
 if __name__ == "__main__":

@@ -68,6 +68,7 @@ struct les_handle {
     double *d_diag = nullptr;
     long long *d_probe_base = nullptr;
     double *d_stage = nullptr;   // 5*max(N) doubles: host transfer staging
+    unsigned long long *d_oob = nullptr; // first out-of-range index (bounds-checked builds)
     int nblk_diag = 0;
     int64_t step = 0;
     std::vector<double> dt;
@@ -197,7 +198,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
 static int storage_prec(int precision) { return precision == LES_FP64 ? LES_FP64 : LES_FP32; }
 
 struct GlobalPlan {
-    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, total;
+    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, o_oob, total;
 };
 
 static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, long long maxN)
@@ -219,6 +220,7 @@ static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, lon
     P.o_pbase = take(sizeof(long long));
     P.o_stage = take(sizeof(double) * 5 * (size_t)maxN);
     P.o_fj = take(sizeof(FusedJet) * 2 * njets);
+    P.o_oob = take(sizeof(unsigned long long));
     P.total = off;
     return P;
 }
@@ -258,6 +260,7 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.hflux = (real *)J.hflux;
     D.rhs = (real *)J.rhs;
     D.inflow_r = J.inflow_r;
+    D.oob = h->d_oob;
     const les_params &p = J.prm;
     D.gamma = p.gamma;
     D.Pr = p.Pr;
@@ -483,6 +486,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     h->d_probe_base = (long long *)(B + GP.o_pbase);
     h->d_stage = (double *)(B + GP.o_stage);
     h->d_fj = (FusedJet *)(B + GP.o_fj);
+    h->d_oob = (unsigned long long *)(B + GP.o_oob);
     h->d_fj1 = h->d_fj + njets;
     for (int j = 0; j < njets; ++j) {
         JetHost &J = h->J[j];
@@ -559,6 +563,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     }
     CK(cudaMemcpyAsync(h->d_maps, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemsetAsync(h->d_level, 0, sizeof(long long), h->st));
+    CK(cudaMemsetAsync(h->d_oob, 0, sizeof(unsigned long long), h->st));
     CK(cudaMemsetAsync(h->d_dt, 0, sizeof(double) * njets, h->st));
     CK(cudaStreamSynchronize(h->st));
     h->dt.assign(njets, 0.0);
@@ -1159,6 +1164,25 @@ extern "C" int les_probe_frames(les_handle *h, int64_t *frames)
 extern "C" int64_t les_last_launch_count(les_handle *h) { return h ? h->last_launches : 0; }
 
 extern "C" const char *les_last_error(les_handle *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" int les_bounds_checking(void)
+{
+#ifdef LES_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" int les_bounds_violation(les_handle *h, uint64_t *out)
+{
+    if (!h || !out) return LES_ERR_ARG;
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_oob, sizeof(v), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *out = (uint64_t)v;
+    return LES_OK;
+}
 
 extern "C" const char *les_describe(les_handle *h)
 {

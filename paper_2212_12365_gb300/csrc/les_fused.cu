@@ -407,6 +407,15 @@ __device__ __forceinline__ D3 deriv_end(int t, const float4 &a1, const float2 &b
 
 } // namespace
 
+// Index checks of a LES_BOUNDS_CHECK build (nothing otherwise): global
+// offsets against the padded point count, shared-memory slots against their
+// tables (point ring 5 NC2 cells, plane tables 2 x (3 or 2) NC1 cells,
+// eta-flux rows 5 TY FX).
+#define CK_G(site, x) LES_BOUNDS(J.oob, (site), (x), J.npts_pad)
+#define CK_RING(x) ((int)LES_BOUNDS(J.oob, 5, (x), 5 * N2))
+#define CK_TAB(x, n) ((int)LES_BOUNDS(J.oob, 6, (x), (n)))
+#define CK_SH(x) ((int)LES_BOUNDS(J.oob, 7, (x), 5 * TY * FX))
+
 template <int TY, bool SEP>
 __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
@@ -543,7 +552,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 if (lc[t] < 0) continue;
-                const long long o = gk * plane + lo2[t];
+                const long long o = CK_G(2, gk * plane + lo2[t]);
 #pragma unroll
                 for (int f = 0; f < 5; ++f) cp_async4(&S.QS[(t * 5 + f) * G_::NT + tid], Qs + f * fs + o);
             }
@@ -568,7 +577,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
             for (int t = 0; t < 9; ++t) m[t] = 0.0f;
             if (!SEP && g_act) {
-                const float4 *mp = F.mp + 4 * (gkG * plane + ocol);
+                const float4 *mp = F.mp + 4 * CK_G(3, gkG * plane + ocol);
                 const float4 a0 = mp[0], a1 = mp[1], a2 = mp[2], a3 = mp[3];
                 m[0] = a0.x; m[1] = a0.y; m[2] = a0.z; m[3] = a0.w;
                 m[4] = a1.x; m[5] = a1.y; m[6] = a1.z; m[7] = a1.w;
@@ -591,7 +600,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
-                    const long long o = gkL * plane + lo2[t];
+                    const long long o = CK_G(2, gkL * plane + lo2[t]);
                     if constexpr (SEP) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
@@ -602,9 +611,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
             if (!SEP && g_act) {
-                S.MA[(rG * 2 + 0) * N1 + c1] = make_float4(m[0], m[1], m[2], m[3]);
-                S.MA[(rG * 2 + 1) * N1 + c1] = make_float4(m[4], m[5], m[6], m[7]);
-                S.MB[rG * N1 + c1] = make_float2(m[8], jinvG);
+                S.MA[CK_TAB((rG * 2 + 0) * N1 + c1, 4 * N1)] = make_float4(m[0], m[1], m[2], m[3]);
+                S.MA[CK_TAB((rG * 2 + 1) * N1 + c1, 4 * N1)] = make_float4(m[4], m[5], m[6], m[7]);
+                S.MB[CK_TAB(rG * N1 + c1, 2 * N1)] = make_float2(m[8], jinvG);
             }
             if (gkL >= 0) {
                 const int sb = sl[5] * N2;
@@ -616,14 +625,14 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     const float u = qv[t][1] * rr, v = qv[t][2] * rr, w = qv[t][3] * rr;
                     const float e = qv[t][4];
                     const float p = FP.gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
-                    S.PA[sb + lc[t]] = make_float4(rho, u, v, w);
-                    S.PB[sb + lc[t]] = make_float2(p, FP.gam * p * rr);
+                    S.PA[CK_RING(sb + lc[t])] = make_float4(rho, u, v, w);
+                    S.PB[CK_RING(sb + lc[t])] = make_float2(p, FP.gam * p * rr);
                 }
             }
             __syncthreads();
             // ---- derivatives, SGS, sensors, lambda-bar of plane kG on R1 (one cell per thread) ----
             if (g_act) {
-                const int s0 = sl[3] * N2 + c2; // plane kG
+                const int s0 = CK_RING(sl[3] * N2 + c2); // plane kG
                 const float4 A0 = S.PA[s0];
                 const float2 B0 = S.PB[s0];
                 D3 dd[3];
@@ -632,9 +641,11 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     const int st = a == 0 ? 1 : C2X;
                     const int tt = a == 0 ? ti : tj;
                     if (tt == 0) {
-                        dd[a] = deriv_central(S.PA[s0 - st], S.PB[s0 - st], B0.x, S.PA[s0 + st], S.PB[s0 + st]);
+                        const int sm = CK_RING(s0 - st), sp = CK_RING(s0 + st);
+                        dd[a] = deriv_central(S.PA[sm], S.PB[sm], B0.x, S.PA[sp], S.PB[sp]);
                     } else {
-                        const int o1 = s0 + (tt - 1) * st, o2 = s0 + tt * st, o3 = s0 + (tt + 1) * st;
+                        const int o1 = CK_RING(s0 + (tt - 1) * st), o2 = CK_RING(s0 + tt * st),
+                                  o3 = CK_RING(s0 + (tt + 1) * st);
                         dd[a] = deriv_end(tt, S.PA[o1], S.PB[o1], S.PA[o2], S.PB[o2], S.PA[o3], S.PB[o3]);
                     }
                 }
@@ -642,11 +653,11 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     // zeta stencil of this plane (uniform): central, or one-sided at an end
                     const int tk = (!pk && gkG == 0) ? 1 : ((!pk && gkG == nk - 1) ? -1 : 0);
                     if (tk == 0) {
-                        const int om = sl[2] * N2 + c2, op = sl[4] * N2 + c2;
+                        const int om = CK_RING(sl[2] * N2 + c2), op = CK_RING(sl[4] * N2 + c2);
                         dd[2] = deriv_central(S.PA[om], S.PB[om], B0.x, S.PA[op], S.PB[op]);
                     } else {
-                        const int o1 = sl[tk > 0 ? 3 : 1] * N2 + c2, o2 = sl[tk > 0 ? 4 : 2] * N2 + c2,
-                                  o3 = sl[tk > 0 ? 5 : 3] * N2 + c2;
+                        const int o1 = CK_RING(sl[tk > 0 ? 3 : 1] * N2 + c2), o2 = CK_RING(sl[tk > 0 ? 4 : 2] * N2 + c2),
+                                  o3 = CK_RING(sl[tk > 0 ? 5 : 3] * N2 + c2);
                         dd[2] = deriv_end(tk, S.PA[o1], S.PB[o1], S.PA[o2], S.PB[o2], S.PA[o3], S.PB[o3]);
                     }
                 }
@@ -698,10 +709,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 const float s01 = sqrt_nonneg(lam[0] * lam[1]), s02 = sqrt_nonneg(lam[0] * lam[2]),
                             s12 = sqrt_nonneg(lam[1] * lam[2]);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) S.GD[(rG * 3 + a) * N1 + c1] = dd[a].d;
-                S.GC[(rG * 2 + 0) * N1 + c1] = make_float4(mu * FP.inv_Re + mus, mu * FP.kap_mol + mus * FP.kap_sgs,
+                for (int a = 0; a < 3; ++a) S.GD[CK_TAB((rG * 3 + a) * N1 + c1, 6 * N1)] = dd[a].d;
+                S.GC[CK_TAB((rG * 2 + 0) * N1 + c1, 4 * N1)] = make_float4(mu * FP.inv_Re + mus, mu * FP.kap_mol + mus * FP.kap_sgs,
                                                            dd[0].nu, lam[0] + s01 + s02);
-                S.GC[(rG * 2 + 1) * N1 + c1] = make_float4(dd[1].nu, lam[1] + s01 + s12, dd[2].nu, lam[2] + s02 + s12);
+                S.GC[CK_TAB((rG * 2 + 1) * N1 + c1, 4 * N1)] = make_float4(dd[1].nu, lam[1] + s01 + s12, dd[2].nu, lam[2] + s02 + s12);
             }
             // No barrier here: the interfaces below read the R1 tables of plane
             // kG only in this thread's own column (the zeta neighbour), written
@@ -725,7 +736,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 const bool do_eta = !first && plane_ok && eta_ok;
                 const bool do_zeta = plane_ok && out_col && (pk || gk < nk - 1);
                 const bool upd = !first && plane_ok && out_col && kU < k1;
-                const long long o = (long long)(plane_ok ? gk : 0) * plane + ocol;
+                const long long o = CK_G(4, (long long)(plane_ok ? gk : 0) * plane + ocol);
                 // separable form: Q(0) of the updated point, in flight during the interfaces
                 float q0s[5] = {0, 0, 0, 0, 0};
                 if (SEP && upd && !rhs_only) {
@@ -743,8 +754,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                         L.T = b.y;
                     }
                     if constexpr (!SEP) {
-                        const float4 u0 = S.MA[(rU * 2 + 0) * N1 + c1], u1 = S.MA[(rU * 2 + 1) * N1 + c1];
-                        const float2 u2 = S.MB[rU * N1 + c1];
+                        const float4 u0 = S.MA[CK_TAB((rU * 2 + 0) * N1 + c1, 4 * N1)],
+                                     u1 = S.MA[CK_TAB((rU * 2 + 1) * N1 + c1, 4 * N1)];
+                        const float2 u2 = S.MB[CK_TAB(rU * N1 + c1, 2 * N1)];
                         L.m[0] = u0.x; L.m[1] = u0.y; L.m[2] = u0.z; L.m[3] = u0.w;
                         L.m[4] = u1.x; L.m[5] = u1.y; L.m[6] = u1.z; L.m[7] = u1.w;
                         L.m[8] = u2.x;
@@ -763,10 +775,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     if (do_xi) {
                         if constexpr (SEP) {
                             const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
-                            fused_iface_sep<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU,
+                            fused_iface_sep<0, TY>(S, FP, L, CK_RING(sU + c2 + 1), CK_RING(sU + c2 - 1),
+                                                   CK_RING(sU + c2 + 2), CK_TAB(c1 + 1, N1), rU,
                                                    xi_lo, xi_hi, hX.x, S.HX[tx + 2].x, hY.x, hY.y, hZ.x, hZ.y, hx);
                         } else {
-                            fused_iface<0, TY>(S, FP, L, sU + c2 + 1, sU + c2 - 1, sU + c2 + 2, c1 + 1, rU, xi_lo,
+                            fused_iface<0, TY>(S, FP, L, CK_RING(sU + c2 + 1), CK_RING(sU + c2 - 1),
+                                               CK_RING(sU + c2 + 2), CK_TAB(c1 + 1, N1), rU, xi_lo,
                                                xi_hi, hx);
                         }
                     }
@@ -776,15 +790,17 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 if (do_eta) {
                     if constexpr (SEP) {
                         const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
-                        fused_iface_sep<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX,
+                        fused_iface_sep<1, TY>(S, FP, L, CK_RING(sU + c2 + C2X), CK_RING(sU + c2 - C2X),
+                                               CK_RING(sU + c2 + 2 * C2X), CK_TAB(c1 + FX, N1),
                                                rU, eta_lo, eta_hi, hY.x, S.HY[ty + 2].x, hX.x, hX.y, hZ.x, hZ.y, hy);
                     } else {
-                        fused_iface<1, TY>(S, FP, L, sU + c2 + C2X, sU + c2 - C2X, sU + c2 + 2 * C2X, c1 + FX, rU,
+                        fused_iface<1, TY>(S, FP, L, CK_RING(sU + c2 + C2X), CK_RING(sU + c2 - C2X),
+                                           CK_RING(sU + c2 + 2 * C2X), CK_TAB(c1 + FX, N1), rU,
                                            eta_lo, eta_hi, hy);
                     }
                 }
 #pragma unroll
-                for (int f = 0; f < 5; ++f) S.SH[(f * TY + ty) * FX + tx] = hy[f];
+                for (int f = 0; f < 5; ++f) S.SH[CK_SH((f * TY + ty) * FX + tx)] = hy[f];
                 {
                     float hz[5] = {0, 0, 0, 0, 0};
                     if (do_zeta) {
@@ -792,10 +808,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                         if constexpr (SEP) {
                             const float4 hX = S.HX[tx + 1], hY = S.HY[ty + 1], hZ = F.h1[2][gk];
                             const float hZR = F.h1[2][gidx(kU + 1, nk, pk)].x;
-                            fused_iface_sep<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
+                            fused_iface_sep<2, TY>(S, FP, L, CK_RING(sl[3] * N2 + c2), CK_RING(sl[1] * N2 + c2),
+                                                   CK_RING(sl[4] * N2 + c2), c1,
                                                    ring2(kU + 1), lo, hi, hZ.x, hZR, hX.x, hX.y, hY.x, hY.y, hz);
                         } else {
-                            fused_iface<2, TY>(S, FP, L, sl[3] * N2 + c2, sl[1] * N2 + c2, sl[4] * N2 + c2, c1,
+                            fused_iface<2, TY>(S, FP, L, CK_RING(sl[3] * N2 + c2), CK_RING(sl[1] * N2 + c2),
+                                               CK_RING(sl[4] * N2 + c2), c1,
                                                ring2(kU + 1), lo, hi, hz);
                         }
                     }
@@ -815,7 +833,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 __syncthreads();
                 if (upd) {
 #pragma unroll
-                    for (int f = 0; f < 5; ++f) R[f] += hy[f] - S.SH[(f * TY + ty - 1) * FX + tx];
+                    for (int f = 0; f < 5; ++f) R[f] += hy[f] - S.SH[CK_SH((f * TY + ty - 1) * FX + tx)];
                     if (rhs_only) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) J.rhs[f * fs + o] = R[f];
@@ -841,6 +859,11 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         }
     }
 }
+
+#undef CK_G
+#undef CK_RING
+#undef CK_TAB
+#undef CK_SH
 
 template <int TY> int fused_prepare()
 {

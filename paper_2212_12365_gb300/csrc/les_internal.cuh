@@ -84,6 +84,9 @@ struct JetDev {
     double bc_g1, bc_rg, bc_cinf; // 1/(gamma-1), 1/gamma, ambient sound speed (1/TR)^1/2
     unsigned long long seed;
     long long npts_pad; // nk*nj*pitch
+    // first out-of-range index met by a kernel of a LES_BOUNDS_CHECK build
+    // (see bounds_ok); unused otherwise
+    unsigned long long *oob;
 };
 
 // Block map of a batched launch: virtual block vb belongs to jet j when
@@ -104,9 +107,41 @@ __device__ __forceinline__ int find_jet(const BlockMap &bm, int vb)
     return lo;
 }
 
+// Index-bounds checking of a debug build (compiled with -DLES_BOUNDS_CHECK,
+// the stand-in for a memory checker): an index outside [0, n) is recorded
+// in *oob as (site << 48) | (index & 2^48-1), first violation wins, and the
+// access is redirected to index 0 instead of faulting.  In a normal build
+// the checks compile to nothing.  Sites: 1 point index (lidx), 2-4 global
+// offsets of the fused stage (state / static record / update), 5-7 its
+// shared-memory slots (point ring / plane tables / eta-flux rows).
+#if defined(LES_BOUNDS_CHECK) && defined(__CUDA_ARCH__)
+__device__ __forceinline__ void bounds_record(unsigned long long *oob, int site, unsigned long long v)
+{
+    if (oob) atomicCAS(oob, 0ull, ((unsigned long long)site << 48) | (v & 0xFFFFFFFFFFFFull));
+}
+__device__ __forceinline__ long long bounds_ok(unsigned long long *oob, int site, long long idx, long long n)
+{
+    if (idx >= 0 && idx < n) return idx;
+    bounds_record(oob, site, (unsigned long long)idx);
+    return 0;
+}
+#define LES_BOUNDS(oob, site, idx, n) bounds_ok((oob), (site), (long long)(idx), (long long)(n))
+#else
+#define LES_BOUNDS(oob, site, idx, n) (idx)
+#endif
+
 template <typename real>
 __host__ __device__ __forceinline__ long long lidx(const JetDev<real> &J, int i, int j, int k)
 {
+#if defined(LES_BOUNDS_CHECK) && defined(__CUDA_ARCH__)
+    // a component out of its axis (recorded as 16-bit i, j, k) could still
+    // land inside the array, so the components are checked
+    if (i < 0 || i >= J.n[0] || j < 0 || j >= J.n[1] || k < 0 || k >= J.n[2]) {
+        bounds_record(J.oob, 1, ((unsigned long long)(k & 0xFFFF) << 32) | ((unsigned long long)(j & 0xFFFF) << 16) |
+                                    (unsigned long long)(i & 0xFFFF));
+        return 0;
+    }
+#endif
     return ((long long)k * J.n[1] + j) * J.pitch + i;
 }
 

@@ -17,7 +17,9 @@ import numpy as np
 from .inputs import FlowParams, GridSpec
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libles.so")
+# LES_LIBRARY selects another in-tree build of the same library (the
+# bounds-checked debug build, _build_bounds/libles.so)
+LIB_PATH = os.environ.get("LES_LIBRARY") or os.path.join(_HERE, "_build", "libles.so")
 
 LES_OK, LES_ERR_ARG, LES_ERR_OOM, LES_ERR_CUDA, LES_ERR_NONFINITE, LES_ERR_TIMEOUT, LES_ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6)
@@ -32,7 +34,8 @@ EXPORTED = [
     "les_set_state_jet", "les_step", "les_get_state", "les_get_state_jet", "les_set_time",
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
-    "les_set_fused_tiling", "les_last_launch_count", "les_diag_sums_noalloc", "les_describe",
+    "les_set_fused_tiling", "les_last_launch_count", "les_bounds_checking", "les_bounds_violation",
+    "les_diag_sums_noalloc", "les_describe",
     "les_last_error", "les_destroy",
 ]
 
@@ -96,6 +99,8 @@ def lib():
         L.les_set_fused_tiling.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.les_last_launch_count.argtypes = [vp]
         L.les_last_launch_count.restype = ctypes.c_int64
+        L.les_bounds_checking.argtypes = []
+        L.les_bounds_violation.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.les_describe.argtypes = [vp]
         L.les_describe.restype = ctypes.c_char_p
@@ -274,6 +279,19 @@ def les_set_fused_tiling(h, ty: int, kc: int):
 
 def les_last_launch_count(h) -> int:
     return int(lib().les_last_launch_count(h))
+
+
+def les_bounds_checking() -> bool:
+    """True for a library built with -DLES_BOUNDS_CHECK."""
+    return bool(lib().les_bounds_checking())
+
+
+def les_bounds_violation(h) -> int:
+    """First out-of-range index met by the handle's kernels ((site << 48) |
+    value), 0 if none (always 0 in a normal build)."""
+    v = ctypes.c_uint64(0)
+    _check(h, lib().les_bounds_violation(h, ctypes.byref(v)))
+    return int(v.value)
 
 
 NOALLOC_MAX_POINTS = 268435456

@@ -41,6 +41,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(les.EXPORTED) == syms
 
 
+def test_bounds_checked_build_loads_and_reports_itself(lib):
+    """The debug build (-DLES_BOUNDS_CHECK) builds, exports the same entry
+    points and says it checks; the normal build says it does not."""
+    from paper_2212_12365_gb300 import build
+    path = build.build(bounds=True)
+    dbg = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(dbg, s), s
+    assert dbg.les_bounds_checking() == 1
+    assert lib.les_bounds_checking() == 0
+    out = ctypes.c_uint64(7)
+    assert lib.les_bounds_violation(None, ctypes.byref(out)) != 0  # NULL handle: LES_ERR_ARG
+
+
 def _desc(spec, **over):
     from paper_2212_12365_gb300 import les
     keep = []
