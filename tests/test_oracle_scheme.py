@@ -30,6 +30,42 @@ def test_rk_polynomial_closed_form():
         assert abs(rk_amplification(z, JAMESON) - g) < 1e-14
 
 
+def test_gaussian_pulse_splits_and_travels_at_sound_speed():
+    """A small Gaussian pressure pulse (rho' = p'/a^2, u' = 0) in a gas at rest
+    splits into two pulses of half the amplitude that travel at +-a: after
+    t = 40 cells / a the right-going peak is within one cell of x0 + a t
+    (the central scheme's group velocity a cos(kh) lags a pulse 8 cells wide
+    by about 0.6 cell there).  Inviscid, fourth-difference dissipation
+    on.  A wrong sound speed, pressure flux or equation of state moves the
+    peak by many cells or changes the split."""
+    n, sigma, x0, eps = 240, 8.0, 60.0, 1e-5
+    spec = I.periodic_box_grid((n, 4, 4))
+    fp = I.FlowParams(Re=math.inf, Cs=0.0, k2=0.0, k4=0.016)
+    g, p = to_oracle(spec, fp)
+    m = oracle.metrics(g)
+    rho0, p0 = 1.0, 1 / GAMMA
+    a = math.sqrt(GAMMA * p0 / rho0)
+    x = spec.x
+    pp = eps * np.exp(-(((x - x0) / sigma) ** 2))
+    prim = _uniform_prim(g.N, rho0, (0, 0, 0), p0)
+    prim[0] += pp / a**2
+    prim[4] += pp
+    q = oracle.qhat_from(g, p, m, prim, True)
+    dt, steps = 0.5, 80
+    out = oracle.state_out(g, p, m, oracle.step(g, p, m, q, steps, 0, dt), True)
+    dp = (out[4] - p0).reshape(4, 4, n)[0, 0]
+    xs = np.arange(n, dtype=float)
+    right = xs > x0
+    i = int(np.argmax(np.where(right, dp, -np.inf)))
+    # parabolic refinement of the peak position
+    c = 0.5 * (dp[i - 1] - dp[i + 1]) / (dp[i - 1] - 2 * dp[i] + dp[i + 1])
+    assert abs(i + c - (x0 + a * steps * dt)) <= 1.0, (i + c, x0 + a * steps * dt)
+    j = int(np.argmax(np.where(~right, dp, -np.inf)))
+    assert abs(j - (x0 - a * steps * dt)) <= 1.5
+    # each half carries half the amplitude (minus a little dispersion/dissipation)
+    assert 0.42 * eps <= dp[i] <= 0.5 * eps and 0.42 * eps <= dp[j] <= 0.5 * eps, (dp[i] / eps, dp[j] / eps)
+
+
 @pytest.mark.parametrize("steps", [1, 3])
 def test_acoustic_wave_semidiscrete_rk(steps):
     """Small right-going acoustic wave on a uniform periodic grid, inviscid, no
