@@ -40,7 +40,7 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
                            "fp32-sep": 14 * 4}
 # DRAM bytes per point of one launch of the dominant kernel, from the ncu
 # captures summarised in profiles/ (None once the kernel changed since).
-TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 95.7}
+TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 95.6}
 # Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
