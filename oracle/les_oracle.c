@@ -64,6 +64,16 @@
  *       lambda-bar is evaluated in its product form lambda_a +
  *       (lambda_a lambda_b)^1/2 + (lambda_a lambda_d)^1/2, which is the
  *       paper's expression for lambda_a > 0 and its limit 0 at lambda_a = 0.
+ *   R18 subsonic jet entrance (Sec. "Entrance Boundary", mach_j < 1): at
+ *       the jet points of the inflow face (profile >= 0.01) u is fixed to
+ *       the profile M_j u~ (plus the u noise of the level), v and w are
+ *       taken from the adjacent interior point, the static temperature is
+ *       the jet total temperature 1 + (gamma-1) M_j^2/2 divided by
+ *       1 + (gamma-1) |u|^2/2 with the face velocity in units of a_j (as
+ *       printed; it gives T = 1 in the undisturbed jet) and
+ *       p = T^(gamma/(gamma-1))/gamma; the paper's "M_inf" in the total
+ *       temperature is read as the jet Mach number.  A supersonic jet keeps
+ *       R15 (all variables from the jet).
  */
 #include <math.h>
 #include <stdint.h>
@@ -678,8 +688,9 @@ static double inflow_profile(const Params *P, double r)
 
 /* Sec. "Entrance Boundary": supersonic jet -> all variables from the jet
  * (here the tanh profile with Crocco-Busemann T, uniform p, and the noise of
- * time level `level`); outside the jet the far-field condition with the xi
- * direction as normal. Returns 1 if the Dirichlet jet state was used. */
+ * time level `level`); subsonic jet -> reading R18; outside the jet the
+ * far-field condition with the xi direction as normal. Returns 1 if a jet
+ * state was used. */
 static int inflow_state(const Grid *g, const Params *P, int j, int k, long level, const double Qe[5],
                         const double n[3], double Qf[5])
 {
@@ -692,6 +703,20 @@ static int inflow_state(const Grid *g, const Params *P, int j, int k, long level
         return 0;
     }
     double gm = P->gamma, M = P->mach_j;
+    if (M < 1.0) {
+        double u = M * ut;
+        if (level > 0) {
+            uint64_t ctr = (((uint64_t)(level - 1) * (uint64_t)g->n[2] + (uint64_t)k) * (uint64_t)g->n[1] +
+                            (uint64_t)j) * 3u;
+            u += P->noise_amp * M * (2.0 * unit_double(splitmix64_at(P->seed, ctr)) - 1.0);
+        }
+        double v = Qe[2] / Qe[0], w = Qe[3] / Qe[0];
+        double Tt = 1.0 + 0.5 * (gm - 1.0) * M * M;
+        double T = Tt / (1.0 + 0.5 * (gm - 1.0) * (u * u + v * v + w * w));
+        double p = pow(T, gm / (gm - 1.0)) / gm;
+        cons_from_prim(P, gm * p / T, u, v, w, p, Qf);
+        return 1;
+    }
     double Tinf = 1.0 / P->TR;
     double T = Tinf * (1.0 - ut) + ut + 0.5 * (gm - 1.0) * M * M * ut * (1.0 - ut);
     double p = 1.0 / gm;

@@ -175,6 +175,81 @@ def test_inflow_face_jet_state_and_noise():
     np.testing.assert_array_equal(q1, oracle.apply_bc(g, P, m, q, 1))
 
 
+def test_subsonic_entrance_isentropic_jet_state():
+    """Subsonic jet entrance (Sec. "Entrance Boundary", reading R18) on the
+    inflow face of a Mach 0.8 jet whose interior carries a transverse flow:
+    - u is the profile M_j u~ at level 0, and at level n its deviation from
+      the profile, over A = noise_amp M_j, is the u noise of the supersonic
+      rule at the same level (same seed and counter);
+    - v, w are those of the adjacent interior point;
+    - every jet point is on the jet's isentrope, p / rho^gamma = 1/gamma
+      (total conditions of the jet, an isentropic expansion);
+    - in the undisturbed core (v = w = 0, u~ = 1, no noise) the state is the
+      jet design state rho = 1, T = 1, p = 1/gamma, u = M_j — the point where
+      the subsonic and the supersonic rules must agree."""
+    spec, _ = I.jet_small()
+    ni = spec.dims[0]
+    face = np.arange(spec.N) % ni == 0
+    r = np.hypot(spec.y[face], spec.z[face])
+    states = {}
+    for M in (0.8, 1.4):
+        fp = I.FlowParams(mach_j=M, seed=9)
+        g, P = to_oracle(spec, fp)
+        m = oracle.metrics(g)
+        prim = I.ambient_primitives(g.N, fp.TR)
+        # a transverse flow in the interior next to the face
+        inner = np.arange(g.N) % ni == 1
+        prim[2][inner] = 0.05 * np.sin(3.0 * spec.y[inner])
+        prim[3][inner] = -0.03 * np.cos(2.0 * spec.z[inner])
+        q = oracle.qhat_from(g, P, m, prim, True)
+        states[M] = (fp, P, [oracle.state_out(g, P, m, oracle.apply_bc(g, P, m, q, lv), True) for lv in (0, 3)],
+                     prim)
+    fp, P, (o0, o3), prim = states[0.8]
+    M = 0.8
+    ut = np.array([oracle.inflow_profile(P, x) for x in r])
+    jet = ut >= 0.01
+    assert jet.sum() > 20 and (~jet).sum() > 20
+    rho, u, v, w, p = (o[face] for o in o0)
+    np.testing.assert_allclose(u[jet], M * ut[jet], rtol=1e-14)  # rho u / rho: a few ulp
+    inner = np.roll(face, 1)  # the i = 1 point of each face point
+    np.testing.assert_allclose(v[jet], prim[2][inner][jet], rtol=1e-14, atol=1e-17)
+    np.testing.assert_allclose(w[jet], prim[3][inner][jet], rtol=1e-14, atol=1e-17)
+    np.testing.assert_allclose(p[jet] / rho[jet] ** GAMMA, 1 / GAMMA, rtol=1e-13)
+    core = jet & (ut > 1 - 1e-12) & (np.abs(v) < 1e-300) & (np.abs(w) < 1e-300)
+    if core.any():
+        np.testing.assert_allclose(rho[core], 1.0, rtol=1e-14)
+        np.testing.assert_allclose(p[core], 1 / GAMMA, rtol=1e-14)
+    # the u noise of level 3 is the supersonic rule's, scaled by M_j
+    u3 = o3[1][face]
+    _, Ps, (_, s3), _ = states[1.4]
+    us3 = s3[1][face]
+    noise_sub = (u3[jet] - M * ut[jet]) / (fp.noise_amp * M)
+    noise_sup = (us3[jet] - 1.4 * ut[jet]) / (fp.noise_amp * 1.4)
+    np.testing.assert_allclose(noise_sub, noise_sup, rtol=0, atol=1e-9)
+    assert np.abs(noise_sub).max() > 0.5
+
+
+def test_subsonic_entrance_core_matches_design_state():
+    """A flat core (u~ = 1 to rounding) with no transverse flow: the subsonic
+    rule gives exactly the jet state of the supersonic rule at TR = 1
+    (rho = T = 1, p = 1/gamma, u = M_j) for any M_j < 1."""
+    spec, _ = I.jet_small()
+    ni = spec.dims[0]
+    face = np.arange(spec.N) % ni == 0
+    r = np.hypot(spec.y[face], spec.z[face])
+    for M in (0.3, 0.9, 0.999):
+        fp = I.FlowParams(mach_j=M, theta=0.01)
+        g, P = to_oracle(spec, fp)
+        m = oracle.metrics(g)
+        q = oracle.qhat_from(g, P, m, I.ambient_primitives(g.N, fp.TR), True)
+        out = oracle.state_out(g, P, m, oracle.apply_bc(g, P, m, q, 0), True)
+        c = r < 0.2
+        assert c.sum() >= 4
+        np.testing.assert_allclose(out[0][face][c], 1.0, rtol=1e-13)
+        np.testing.assert_allclose(out[1][face][c], M, rtol=1e-13)
+        np.testing.assert_allclose(out[4][face][c], 1 / GAMMA, rtol=1e-13)
+
+
 def test_splitmix64_reference_vectors():
     path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_reference.txt")
     rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
