@@ -56,7 +56,9 @@ extern "C" {
  * only (jet axis along x at y = z = 0). */
 #define LES_BC_PERIODIC 0   /* Sec. "Periodic Boundary Condition", modulo indexing */
 #define LES_BC_FARFIELD 1   /* Sec. "Far Field Boundary", Riemann invariants */
-#define LES_BC_INFLOW_JET 2 /* Sec. "Entrance Boundary", supersonic jet + far field */
+#define LES_BC_INFLOW_JET 2 /* Sec. "Entrance Boundary": jet (supersonic: all variables
+                               imposed; subsonic: u imposed, v and w from the interior,
+                               T and p from the jet's total conditions) + far field */
 #define LES_BC_EXIT 3       /* Sec. "Exit Boundary Condition" */
 #define LES_BC_CENTERLINE 4 /* Sec. "Centerline Boundary Condition": the j- face is the
                                degenerate axis of a polar mesh (J^-1 = 0 allowed there; k
@@ -110,7 +112,7 @@ typedef struct les_params {
     double Cs;        /* Smagorinsky constant (0.17) */
     double k2, k4;    /* Turkel-Vatsa constants (0.25, 0.016) */
     double Re;        /* rho_j a_j D / mu_j; INFINITY = inviscid */
-    double mach_j;    /* jet Mach number (>= 1 for LES_BC_INFLOW_JET) */
+    double mach_j;    /* jet Mach number (> 0; < 1 selects the subsonic entrance) */
     double TR;        /* T_j / T_inf (PR = 1: p_j = p_inf) */
     double T_inf_dim; /* ambient temperature in K for Sutherland (288.15) */
     double S1_dim;    /* Sutherland constant in K (110.4) */
@@ -142,7 +144,7 @@ size_t les_workspace_bytes(const les_grid_desc *g);
  * form and J^-1 in FP64.  stream: a cudaStream_t (NULL = default stream).
  * On success *out owns all device memory of the solver until les_destroy.
  * Errors: LES_ERR_ARG (dims < 4, inconsistent periodic/BC flags, INFLOW_JET
- * off the i- face, Mach < 1 with INFLOW_JET, non-positive J^-1),
+ * off the i- face, mach_j <= 0 with INFLOW_JET, non-positive J^-1),
  * LES_ERR_OOM, LES_ERR_CUDA. */
 int les_create_grid(const les_grid_desc *g, const les_params *p, void *stream, les_handle **out);
 

@@ -136,8 +136,7 @@ static std::string validate(const les_grid_desc *g, const les_params *p)
         if (t == LES_BC_CENTERLINE && f != 2) return "CENTERLINE is allowed on the j- face only";
         if (t == LES_BC_CENTERLINE && !g->periodic[2]) return "CENTERLINE needs a periodic (azimuthal) k axis";
     }
-    if (g->face_bc[0] == LES_BC_INFLOW_JET && !(p->mach_j >= 1.0))
-        return "INFLOW_JET needs a supersonic jet (mach_j >= 1)";
+    if (g->face_bc[0] == LES_BC_INFLOW_JET && !(p->mach_j > 0.0)) return "INFLOW_JET needs mach_j > 0";
     if (!(p->gamma > 1.0) || !(p->Pr > 0) || !(p->Pr_sgs > 0) || !(p->Re > 0) || !(p->Cs >= 0) ||
         !(p->k2 >= 0) || !(p->k4 >= 0) || !(p->TR > 0) || !(p->T_inf_dim > 0) || !(p->theta > 0) ||
         !(p->cfl > 0) || !(p->dt >= 0))

@@ -451,10 +451,35 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
             const int jj = qf[1], kk = qf[2];
             const T rr = (T)J.inflow_r[(long long)kk * J.n[1] + jj];
             const T ut = T(0.5) * (T(1) + tanh((T(0.5) - rr) / (T(2) * (T)J.theta)));
+            const T M = (T)J.mach;
             if (ut < T(0.01)) {
                 bc_farfield<T, real>(k, Qe, n, Qf);
+            } else if (M < T(1)) {
+                // Sec. "Entrance Boundary", subsonic entrance: u fixed (profile
+                // and the u noise of the level), v and w from the interior
+                // point, T from the jet's total temperature 1 + (gamma-1) M^2/2
+                // with the face velocity in units of a_j, p = T^(gamma/(gamma-1))/gamma
+                T u = M * ut;
+                if (level > 0) {
+                    const unsigned long long ctr =
+                        (((unsigned long long)(level - 1) * (unsigned long long)J.n[2] + (unsigned long long)kk) *
+                             (unsigned long long)J.n[1] +
+                         (unsigned long long)jj) * 3ull;
+                    const double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
+                    u += (T)(J.noise_amp * J.mach * (2.0 * h - 1.0));
+                }
+                const T rre = T(1) / Qe[0];
+                const T v = Qe[2] * rre, w = Qe[3] * rre;
+                const T Ttot = T(1) + T(0.5) * (g - T(1)) * M * M;
+                const T Ts = Ttot / (T(1) + T(0.5) * (g - T(1)) * (u * u + v * v + w * w));
+                PrimT<T> s;
+                s.p = bc_pow<real>(Ts, g * k.g1) * k.rg;
+                s.rho = g * s.p / Ts;
+                s.u[0] = u;
+                s.u[1] = v;
+                s.u[2] = w;
+                cons_t(s, k, Qf);
             } else {
-                const T M = (T)J.mach;
                 const T Tt = (T(1) / (T)J.TR) * (T(1) - ut) + ut + T(0.5) * (g - T(1)) * M * M * ut * (T(1) - ut);
                 PrimT<T> s;
                 s.p = T(1) / g;
