@@ -47,7 +47,14 @@
  *   R12 Smagorinsky filter width Delta = (J^-1)^(1/3).
  *   R13 RK on Qhat = J^-1 Q with RHS = sum of interface-flux differences.
  *   R14 R+ = q_ne + 2 c_e/(gamma-1); velocity corrected along the unit
- *       outward normal of the face.
+ *       outward normal of the face.  The paper's subsonic exit and entrance
+ *       ranges 0 < q_ne/a_e < 1 and -1 < q_ne/a_e < 0 leave q_ne = 0 open;
+ *       a normal Mach number within 1e-8 of zero counts as zero and takes
+ *       the exit side, so that a fluid at rest, or the first weak waves
+ *       reaching a boundary from it (where q_ne crosses zero at rounding
+ *       level), picks the same branch in every evaluation order; the two
+ *       branches differ there by the tangential velocity and entropy of
+ *       such waves only.
  *   R15 inflow: tanh profile of momentum thickness theta, Crocco-Busemann
  *       temperature, uniform pressure, per-step SplitMix64 velocity noise,
  *       Dirichlet where the profile is >= 0.01, far field elsewhere.
@@ -642,7 +649,7 @@ static void farfield_state(const Params *P, const double Qe[5], const double n[3
     if (Mn >= 1.0) { /* supersonic exit: extrapolate everything */
         for (int f = 0; f < NF; f++) Qf[f] = Qe[f];
         return;
-    } else if (Mn >= 0.0) { /* subsonic exit: entropy + tangential velocity from inside */
+    } else if (Mn >= -1e-8) { /* subsonic exit (and q_n = 0, reading R14): entropy + tangential velocity from inside */
         for (int c = 0; c < 3; c++) vel[c] = ue[c] + (qnf - qne) * n[c];
         rho = pow(pow(rhoe, g) * cf * cf / (g * pe), 1.0 / (g - 1.0));
     } else if (Mn > -1.0) { /* subsonic entrance: from the freestream */

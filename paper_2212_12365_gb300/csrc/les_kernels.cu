@@ -333,7 +333,10 @@ __device__ void bc_farfield(const BcK<T> &k, const T Qe[5], const T n[3], T Qf[5
         cons_t(f, k, Qf);
         return;
     }
-    if (mn >= T(0)) { // subsonic outflow: entropy and tangential velocity from inside
+    // subsonic outflow, and |M_n| <= 1e-8 (q_n = 0 up to the rounding of weak
+    // waves, which the paper's ranges leave open): entropy and tangential
+    // velocity from inside
+    if (mn >= T(-1e-8)) {
         // rho_f = (rho_e^gamma c_f^2 / (gamma p_e))^(1/(gamma-1)), gamma p_e = rho_e c_e^2
         for (int c = 0; c < 3; ++c) f.u[c] = e.u[c] + (qnf - qne) * n[c];
         f.rho = bc_pow<P>(bc_pow<P>(e.rho, g) * cf * cf * (rr * rce * rce), k.g1);

@@ -274,22 +274,51 @@ def cylinder_points(r: float, n_theta: int, n_x: int, x0: float, x1: float) -> n
     return np.stack([X.reshape(-1), (r * np.cos(TH)).reshape(-1), (r * np.sin(TH)).reshape(-1)])
 
 
-def polar_jet_grid(ni: int, nj: int, nk: int, Lx: float, R: float, growth: float = 3.0) -> GridSpec:
-    """The paper's jet mesh topology (Sec. "Mesh Generation"): a 2-D (x, r) mesh
-    rotated about the x axis.  i: axial, uniform on [0, Lx]; j: radial from the
-    centerline r = 0 (a degenerate line, J^-1 = 0) to R, spacing growing
-    geometrically-like with r(t) = R t (1 + growth t) / (1 + growth); k:
-    azimuthal, nk unique angles 2 pi k / nk (periodic, no duplicated point).
+def polar_jet_grid(ni: int, nj: int, nk: int, Lx: float, R: float, spacing_ratio: float = 6.0,
+                   width: float = 0.5, spreading: float = 0.094, x_developed: float = 20.0) -> GridSpec:
+    """The paper's jet mesh (Sec. "Mesh Generation"): a 2-D (x, r) mesh
+    refined with hyperbolic tangents, rotated about the x axis.
+    - i, axial: x = Lx (1 - tanh(1.2 (1 - s)) / tanh(1.2)), s uniform on
+      [0, 1]: finest at the jet entrance x = 0, coarsening downstream.
+    - j, radial, from the centerline r = 0 (a degenerate line, J^-1 = 0) to
+      R: at every station the spacing is h (1 + (q - 1) tanh(|r - r_s| / w)),
+      q = spacing_ratio, w = width, finest on the slip line r_s(x) = 1/2,
+      which moves outward at the shear-layer growth rate `spreading` beyond
+      x = x_developed (the self-similar region), and h is scaled so that the
+      last point is r = R; the radial lines therefore bend with x.
+    - k, azimuthal: nk unique angles 2 pi k / nk (periodic, no duplicated
+      point).
     Faces: jet inflow at x = 0, exit at x = Lx, centerline at j = 0, far field
-    at r = R."""
-    x1 = np.linspace(0.0, Lx, ni)
-    t = np.linspace(0.0, 1.0, nj)
-    r1 = R * t * (1.0 + growth * t) / (1.0 + growth)
+    at r = R.  (The paper gives the ingredients, not the functions: these are
+    this package's choice.)"""
+    s = np.linspace(0.0, 1.0, ni)
+    x1 = Lx * (1.0 - np.tanh(1.2 * (1.0 - s)) / np.tanh(1.2))
+    rs = 0.5 + spreading * np.maximum(0.0, x1 - x_developed)
+
+    def march(c):
+        # radial coordinates of all stations for spacing scale c (midpoint rule)
+        r = np.zeros((nj, ni))
+        h = lambda rr: c * (1.0 + (spacing_ratio - 1.0) * np.tanh(np.abs(rr - rs) / width))
+        for jj in range(nj - 1):
+            r[jj + 1] = r[jj] + h(r[jj] + 0.5 * h(r[jj]))
+        return r
+
+    lo = np.zeros(ni)
+    hi = np.full(ni, R)
+    for _ in range(80):  # bisection on the scale of every station at once
+        mid = 0.5 * (lo + hi)
+        over = march(mid)[-1] > R
+        hi = np.where(over, mid, hi)
+        lo = np.where(over, lo, mid)
+    r2 = march(0.5 * (lo + hi))
+    r2 *= R / r2[-1]  # the last point exactly on r = R
+    r2[0] = 0.0
     th = 2.0 * np.pi * np.arange(nk) / nk
     K, J, Iax = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
     x = x1[Iax].reshape(-1)
-    y = (r1[J] * np.cos(th[K])).reshape(-1)
-    z = (r1[J] * np.sin(th[K])).reshape(-1)
+    rr = r2[J, Iax]
+    y = (rr * np.cos(th[K])).reshape(-1)
+    z = (rr * np.sin(th[K])).reshape(-1)
     return GridSpec(x=x, y=y, z=z, dims=(ni, nj, nk), periodic=(0, 0, 1),
                     shift=np.zeros((3, 3)),
                     bc=(BC_INFLOW_JET, BC_EXIT, BC_CENTERLINE, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC))

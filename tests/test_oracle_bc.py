@@ -267,3 +267,23 @@ def test_boundary_conditions_keep_ambient_box():
     q = oracle.qhat_from(g, P, m, I.ambient_primitives(g.N, 1.6), True)
     q1 = oracle.apply_bc(g, P, m, q, 3)
     np.testing.assert_allclose(q1, q, rtol=1e-13, atol=1e-15)
+
+
+def test_farfield_zero_normal_velocity_takes_the_exit_branch():
+    """Reading R14: the paper's subsonic ranges leave q_n = 0 open; a normal
+    Mach number within 1e-8 of zero takes the exit side (entropy and
+    tangential velocity from inside), one beyond it the entrance side."""
+    P = _params(1.0)
+    n = np.array([-1.0, 0.0, 0.0])
+    c = math.sqrt(GAMMA * (1 / GAMMA) / 1.0)
+    for Mn, exit_side in ((0.0, True), (-5e-9, True), (5e-9, True), (-3e-8, False)):
+        u = np.array([-Mn * c, 0.02, -0.01])  # q_n = u . n = Mn c
+        rho, p = 1.1, 1 / GAMMA * 1.05
+        Qf = oracle.face_state(P, "farfield", _cons(rho, u, p), n)
+        rf, uf, pf = _prim(Qf)
+        tang = uf - (uf @ n) * n
+        if exit_side:
+            np.testing.assert_allclose(tang, u - (u @ n) * n, atol=1e-15)
+            assert pf / rf**GAMMA == pytest.approx(p / rho**GAMMA, rel=1e-12)
+        else:
+            np.testing.assert_allclose(tang, 0.0, atol=1e-15)

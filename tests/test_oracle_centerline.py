@@ -21,8 +21,8 @@ from helpers import to_oracle
 from paper_2212_12365_gb300 import inputs as I
 
 
-def _setup(dims=(12, 9, 16), Re=1e3):
-    spec = I.polar_jet_grid(*dims, 6.0, 3.0)
+def _setup(dims=(12, 9, 16), Re=1e3, Lx=6.0):
+    spec = I.polar_jet_grid(*dims, Lx, 3.0)
     fp = I.FlowParams(Re=Re)
     g, p = to_oracle(spec, fp)
     return spec, fp, g, p, oracle.metrics(g)
@@ -36,9 +36,10 @@ def test_polar_axis_degenerate():
     assert J[:, 1:, :].min() > 0.0
 
 
+@pytest.mark.parametrize("Lx", [6.0, 30.0])  # 30: radial lines bend past x = 20
 @pytest.mark.parametrize("vel", [(1.4, 0.0, 0.0), (1.2, 0.3, -0.2)])
-def test_polar_freestream_preserved(vel):
-    spec, fp, g, p, m = _setup()
+def test_polar_freestream_preserved(vel, Lx):
+    spec, fp, g, p, m = _setup(Lx=Lx)
     prim = np.zeros((5, spec.N))
     prim[0] = 1.0
     prim[1:4] = np.array(vel)[:, None]
