@@ -52,7 +52,9 @@ extern "C" {
 
 /* Face boundary conditions (Sec. "Boundary Conditions").  Faces are ordered
  * i-, i+, j-, j+, k-, k+.  PERIODIC must be set on both faces of an axis
- * declared periodic and nowhere else.  INFLOW_JET is allowed on the i- face
+ * declared periodic and nowhere else; a periodic axis lists its unique planes
+ * (the paper's overlapping last plane, equal to the first plus the period
+ * shift, is rejected: drop it).  INFLOW_JET is allowed on the i- face
  * only (jet axis along x at y = z = 0). */
 #define LES_BC_PERIODIC 0   /* Sec. "Periodic Boundary Condition", modulo indexing */
 #define LES_BC_FARFIELD 1   /* Sec. "Far Field Boundary", Riemann invariants */
@@ -143,7 +145,8 @@ size_t les_workspace_bytes(const les_grid_desc *g);
  * the nine metric cofactors J^-1 d(xi,eta,zeta)/d(x,y,z) in conservative
  * form and J^-1 in FP64.  stream: a cudaStream_t (NULL = default stream).
  * On success *out owns all device memory of the solver until les_destroy.
- * Errors: LES_ERR_ARG (dims < 4, inconsistent periodic/BC flags, INFLOW_JET
+ * Errors: LES_ERR_ARG (dims < 4, inconsistent periodic/BC flags, a periodic
+ * axis in the overlapping form, INFLOW_JET
  * off the i- face, mach_j <= 0 with INFLOW_JET, non-positive J^-1),
  * LES_ERR_OOM, LES_ERR_CUDA. */
 int les_create_grid(const les_grid_desc *g, const les_params *p, void *stream, les_handle **out);

@@ -129,6 +129,32 @@ static std::string validate(const les_grid_desc *g, const les_params *p)
         if (g->periodic[a] && !(pf && pb)) return "periodic axis needs PERIODIC on both faces";
         if (!g->periodic[a] && (pf || pb)) return "PERIODIC face on a non-periodic axis";
     }
+    // the paper's overlapping form of a periodic axis (Sec. "Periodic Boundary
+    // Condition": the last plane repeats the first) would give a zero-width
+    // cell; this library takes the unique planes only
+    {
+        const int n[3] = {g->ni, g->nj, g->nk};
+        for (int a = 0; a < 3; ++a) {
+            if (!g->periodic[a]) continue;
+            double dmax = 0.0, ext = 0.0;
+            const long long np = (long long)n[0] * n[1] * n[2];
+            for (long long l = 0; l < np; ++l) {
+                const long long q[3] = {l % n[0], (l / n[0]) % n[1], l / ((long long)n[0] * n[1])};
+                if (q[a] != 0) continue;
+                long long r[3] = {q[0], q[1], q[2]};
+                r[a] = n[a] - 1;
+                const long long lr = (r[2] * n[1] + r[1]) * n[0] + r[0];
+                const double *X[3] = {g->x, g->y, g->z};
+                for (int c = 0; c < 3; ++c) {
+                    dmax = std::max(dmax, std::fabs(X[c][lr] - (X[c][l] + g->period_shift[a][c])));
+                    ext = std::max(ext, std::fabs(X[c][l]) + std::fabs(g->period_shift[a][c]));
+                }
+            }
+            if (dmax <= 1e-12 * std::max(ext, 1.0))
+                return "periodic axis " + std::to_string(a) +
+                       " repeats its first plane as its last (overlapping form): pass the unique planes";
+        }
+    }
     for (int f = 0; f < 6; ++f) {
         int t = g->face_bc[f];
         if (t < LES_BC_PERIODIC || t > LES_BC_CENTERLINE) return "unknown face boundary condition";

@@ -324,6 +324,28 @@ def polar_jet_grid(ni: int, nj: int, nk: int, Lx: float, R: float, spacing_ratio
                     bc=(BC_INFLOW_JET, BC_EXIT, BC_CENTERLINE, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC))
 
 
+def unique_periodic_planes(spec: GridSpec, tol: float = 1e-12) -> GridSpec:
+    """Convert a grid in the paper's overlapping periodic form (Sec. "Periodic
+    Boundary Condition": the last plane of a periodic axis repeats the first,
+    shifted by the period) to the form the library takes, the unique planes:
+    the repeated last plane of every such axis is dropped."""
+    ni, nj, nk = spec.dims
+    X = [c.reshape(nk, nj, ni) for c in (spec.x, spec.y, spec.z)]
+    dims = [ni, nj, nk]
+    for a in range(3):
+        if not spec.periodic[a]:
+            continue
+        ax = 2 - a  # array axis of grid axis a ([k][j][i] layout)
+        first = [np.take(c, 0, axis=ax) for c in X]
+        last = [np.take(c, dims[a] - 1, axis=ax) for c in X]
+        scale = max(1.0, max(np.abs(f).max() for f in first))
+        if max(np.abs(l - (f + spec.shift[a][c])).max() for c, (f, l) in enumerate(zip(first, last))) <= tol * scale:
+            X = [np.delete(c, dims[a] - 1, axis=ax) for c in X]
+            dims[a] -= 1
+    return GridSpec(x=X[0].reshape(-1).copy(), y=X[1].reshape(-1).copy(), z=X[2].reshape(-1).copy(),
+                    dims=tuple(dims), periodic=spec.periodic, shift=spec.shift, bc=spec.bc)
+
+
 def curved_periodic_grid(n: tuple, L: float = 1.0, A: float = 0.04) -> GridSpec:
     """Fully periodic curvilinear grid with a FIXED physical displacement of
     amplitude A (independent of the resolution, for refinement studies):

@@ -100,3 +100,42 @@ def test_workspace_size_query(lib):
     b32 = les.les_workspace_bytes(spec, les.LES_FP32)
     # state, metrics, scratch: at least 50 values per point
     assert b64 > 50 * 8 * spec.N and b32 > 50 * 4 * spec.N and b64 > b32
+
+
+def _overlapping_polar(ni=12, nj=8, nk=16):
+    """The paper's overlapping azimuthal form of the polar mesh: nk + 1 planes,
+    the last at 2 pi (= the first)."""
+    g = I.polar_jet_grid(ni, nj, nk, 6.0, 3.0)
+    X = [c.reshape(nk, nj, ni) for c in (g.x, g.y, g.z)]
+    X = [np.concatenate([c, c[:1]], axis=0) for c in X]
+    return I.GridSpec(x=X[0].reshape(-1), y=X[1].reshape(-1), z=X[2].reshape(-1), dims=(ni, nj, nk + 1),
+                      periodic=g.periodic, shift=g.shift, bc=g.bc), g
+
+
+def test_overlapping_periodic_form_rejected_and_converted(lib):
+    """A periodic axis given in the paper's overlapping form (last plane =
+    first plane + period shift) is rejected before any device work, with a
+    message saying so; inputs.unique_periodic_planes turns it into the mesh
+    the library takes, which is the unique-plane polar mesh itself."""
+    from paper_2212_12365_gb300 import les
+    over, unique = _overlapping_polar()
+    keep = []
+    d = les.make_desc(over, les.LES_FP64, keep)
+    h = ctypes.c_void_p()
+    rc = lib.les_create_grid(ctypes.byref(d), ctypes.byref(les.make_params(I.FlowParams())), None, ctypes.byref(h))
+    assert rc == les.LES_ERR_ARG
+    assert b"overlapping" in lib.les_last_error(None)
+    conv = I.unique_periodic_planes(over)
+    assert conv.dims == unique.dims
+    for a, b in ((conv.x, unique.x), (conv.y, unique.y), (conv.z, unique.z)):
+        np.testing.assert_array_equal(a, b)
+    # a translational period: the repeated plane carries the shift
+    box = I.periodic_box_grid((6, 5, 4), h=(1.0, 1.0, 1.0))
+    ni, nj, nk = box.dims
+    X = [c.reshape(nk, nj, ni) for c in (box.x, box.y, box.z)]
+    X = [np.concatenate([c, c[:, :, :1] + box.shift[0][q]], axis=2) for q, c in enumerate(X)]
+    over_box = I.GridSpec(x=X[0].reshape(-1), y=X[1].reshape(-1), z=X[2].reshape(-1), dims=(ni + 1, nj, nk),
+                          periodic=box.periodic, shift=box.shift, bc=box.bc)
+    conv = I.unique_periodic_planes(over_box)
+    assert conv.dims == box.dims
+    np.testing.assert_array_equal(conv.x, box.x)
