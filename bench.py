@@ -447,6 +447,45 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# the paper's ten meshes (n_xi axial, n_eta radial, n_zeta azimuthal; Table
+# "Mesh information"), run here as tanh-refined polar jet meshes of 30D x 12D
+PAPER_MESHES = [(200, 150, 40), (400, 150, 40), (800, 150, 40), (400, 75, 40), (400, 300, 40),
+                (400, 150, 10), (400, 150, 60), (800, 300, 120), (200, 75, 40), (200, 75, 20)]
+
+
+def run_sweep(args):
+    """Throughput over the paper's mesh sizes, FP64 and FP32, one JSON line
+    ({"sweep": [...]}): per mesh the device rate of `steps` timed steps after
+    `warmup` steps from the ambient start (CUDA events on the solver's
+    stream)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2212_12365_gb300 import build, les
+    build.build()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n, dims in enumerate(PAPER_MESHES, start=1):
+        spec = I.polar_jet_grid(*dims, 30.0, 12.0)
+        fp = I.FlowParams(seed=n)
+        row = {"mesh": n, "dims": list(dims), "points": spec.N}
+        for name, P in (("fp64", les.LES_FP64), ("fp32", les.LES_FP32)):
+            s = les.Solver(spec, fp, P, stream=les.ctypes.c_void_p(stream.cuda_stream))
+            s.set_state(I.ambient_primitives(spec.N, fp.TR), les.LES_STATE_PRIMITIVE)
+            s.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            row[name] = {"value": spec.N * 5 / (ms / 1e3), "ms_per_step": ms, "stage": les.les_describe(s.h)}
+            s.close()
+        rows.append(row)
+    print(json.dumps({"metric": "grid-point-stage updates/s", "unit": "grid-point-stage updates/s",
+                      "data": "synthetic", "sweep": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,10 +502,14 @@ def main():
     ap.add_argument("--tiling", default=None,
                     help="TY,KC: fix the fused FP32 stage's tile height and k-chunk (0 = balanced) "
                          "instead of autotuning")
+    ap.add_argument("--sweep", action="store_true",
+                    help="throughput over the paper's ten mesh sizes (polar meshes), FP64 and FP32")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
