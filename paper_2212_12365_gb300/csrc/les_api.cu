@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -972,25 +973,48 @@ template <typename real> static int residual_of_jet(les_handle *h, int jet)
 }
 
 // Autotuner of the fused stage: time (tile height, k-chunk) candidates with
-// residual launches on the current state and keep the fastest; the choice is
-// cached per set of grid shapes for the process.
+// real stage launches on the current state and keep the fastest; the choice
+// is cached per device and set of grid shapes for the process (under a lock:
+// handles may be stepped from several host threads; the timing itself runs
+// outside it, so two threads may tune the same key, and the first result
+// stays).
 static std::map<std::string, std::pair<int, int>> g_tune_cache;
+static std::mutex g_tune_mu;
+
+namespace {
+struct EventPair { // destroyed on every return path
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair()
+    {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+} // namespace
 
 static int autotune_fused(les_handle *h)
 {
-    std::string key;
+    std::string key = "dev" + std::to_string(h->dev) + ":";
     for (auto &J : h->J)
         key += std::to_string(J.n[0]) + "x" + std::to_string(J.n[1]) + "x" + std::to_string(J.n[2]) + "p" +
                std::to_string(J.per[0] * 4 + J.per[1] * 2 + J.per[2]) + (h->sep ? "s;" : ";");
-    auto it = g_tune_cache.find(key);
-    if (it == g_tune_cache.end()) {
+    std::pair<int, int> pick{8, 48};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            pick = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
         const int tys[2] = {16, 8};
         const int kcs[7] = {8, 16, 24, 48, 96, 100000, 0}; // 0: balanced tile-plane ranges
         float best = 1e30f;
-        std::pair<int, int> pick{8, 48};
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
+        EventPair ev;
+        CK(cudaEventCreate(&ev.e0));
+        CK(cudaEventCreate(&ev.e1));
         for (int ty : tys)
             for (int kc : kcs) {
                 int rc = set_fused_tiling(h, ty, kc);
@@ -998,25 +1022,24 @@ static int autotune_fused(les_handle *h)
                 // real stage launches from Q(0) into the first stage register,
                 // which holds no state between steps
                 fused_launch(h, -1, 0, 1, 0, 0, h->st); // warm-up
-                CK(cudaEventRecord(e0, h->st));
+                CK(cudaEventRecord(ev.e0, h->st));
                 for (int rep = 0; rep < 3; ++rep) fused_launch(h, -1, 0, 1, 0, 0, h->st);
-                CK(cudaEventRecord(e1, h->st));
-                CK(cudaEventSynchronize(e1));
+                CK(cudaEventRecord(ev.e1, h->st));
+                CK(cudaEventSynchronize(ev.e1));
                 float ms = 0;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
+                CK(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
                 if (ms < best) {
                     best = ms;
                     pick = {ty, kc};
                 }
             }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        it = g_tune_cache.emplace(key, pick).first;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        pick = g_tune_cache.emplace(key, pick).first->second;
     }
-    h->tune_note = "ty=" + std::to_string(it->second.first) + " kc=" +
-                   (it->second.second == 0 ? std::string("balanced") : std::to_string(it->second.second)) +
+    h->tune_note = "ty=" + std::to_string(pick.first) + " kc=" +
+                   (pick.second == 0 ? std::string("balanced") : std::to_string(pick.second)) +
                    " (tuned over ty {16,8} x kc {8,16,24,48,96,all,balanced})";
-    return set_fused_tiling(h, it->second.first, it->second.second);
+    return set_fused_tiling(h, pick.first, pick.second);
 }
 
 template <typename real> static int diag_impl(les_handle *h, int jet, les_diag *d)

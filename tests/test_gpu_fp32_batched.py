@@ -225,3 +225,30 @@ def test_fp32_unscaled_store_state_and_diagnostics(prec):
     qh = oracle.qhat_from(g, p, m, qc, False)
     mag = np.abs(qh).sum(axis=1)
     assert np.all(np.abs(d["sum_qhat"] - dor["sum_qhat"]) <= 1e-13 * mag), (d["sum_qhat"], dor["sum_qhat"])
+
+
+def test_handles_stepped_from_two_host_threads():
+    """Two FP32 handles of new grid shapes stepped at the same time from two
+    host threads (both run the autotuner and share its cache): both finish
+    with the state a single-threaded run gives."""
+    import threading
+    shapes = [I.jet_grid(29 + 2 * t, 21, 17, 8.0, 6.0, 6.0, 0.15, 0.18) for t in range(2)]
+    fp = I.FlowParams(Re=1e4)
+
+    def run(spec, out, idx):
+        s = les.Solver(spec, fp, les.LES_FP32)
+        s.set_state(I.smooth_random_primitives(spec, 60 + idx, amp=0.05))
+        s.step(3)
+        out[idx] = s.get_state(les.LES_STATE_RAW)
+        s.close()
+
+    res = [None, None]
+    th = [threading.Thread(target=run, args=(shapes[i], res, i)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i in range(2):
+        ref = [None, None]
+        run(shapes[i], ref, i)
+        np.testing.assert_array_equal(res[i], ref[i])
