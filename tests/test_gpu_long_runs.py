@@ -107,9 +107,9 @@ def test_paper_scale_fp32_error_100_and_1000_steps(fp64_run):
     ein = np.sqrt((d.reshape(5, -1) ** 2).sum(axis=1)) / den
     print("fp32 vs fp64 rel L2 per field, 100 steps:", e100, " 1000 steps:", e1000, " interior:", ein)
     assert np.all(np.isfinite(q))
-    assert np.all(e100[[0, 1, 4]] <= 1e-5) and np.all(e100 <= 5e-5), e100
+    assert np.all(e100 <= 1e-5), e100
     assert np.all(e1000 <= 1e-3), e1000
-    assert np.all(ein[[0, 1, 4]] <= 1e-5) and np.all(ein <= 2e-5), ein
+    assert np.all(ein <= 1e-5), ein
 
 
 def test_large_fp32_500_steps_with_probe():
