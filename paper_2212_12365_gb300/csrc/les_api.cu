@@ -70,6 +70,7 @@ struct les_handle {
     long long *d_probe_base = nullptr;
     double *d_stage = nullptr;   // 5*max(N) doubles: host transfer staging
     unsigned long long *d_oob = nullptr; // first out-of-range index (bounds-checked builds)
+    CUtensorMap *d_tmap = nullptr; // per jet: TMA maps of the 3 state registers for TY 8 and 16
     int nblk_diag = 0;
     int64_t step = 0;
     std::vector<double> dt;
@@ -224,7 +225,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
 static int storage_prec(int precision) { return precision == LES_FP64 ? LES_FP64 : LES_FP32; }
 
 struct GlobalPlan {
-    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, o_oob, total;
+    size_t o_jets, o_maps, o_dt, o_level, o_bits, o_part, o_diag, o_pbase, o_stage, o_fj, o_oob, o_tmap, total;
 };
 
 static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, long long maxN)
@@ -247,6 +248,7 @@ static GlobalPlan plan_global(int njets, size_t jetdev_bytes, int nblk_diag, lon
     P.o_stage = take(sizeof(double) * 5 * (size_t)maxN);
     P.o_fj = take(sizeof(FusedJet) * 2 * njets);
     P.o_oob = take(sizeof(unsigned long long));
+    P.o_tmap = take(sizeof(CUtensorMap) * 6 * njets);
     P.total = off;
     return P;
 }
@@ -437,6 +439,48 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
         launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal, st);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links no driver library); null if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    return fn;
+}
+
+// TMA maps of one FP32 jet's three state registers for the fused stage's
+// staging box (5 fields x 1 plane x (TY + 2) rows x 40 columns) at TY = 8 and
+// 16: tensor [field][k][j][i] with the padded row and field strides, columns
+// beyond ni read as zero.  Returns false if the encoder refuses.
+static bool make_state_maps(const JetHost &J, CUtensorMap out[6])
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)J.n[0], (cuuint64_t)J.n[1], (cuuint64_t)J.n[2], 5};
+    const cuuint64_t strides[3] = {(cuuint64_t)J.pitch * 4, (cuuint64_t)J.pitch * J.n[1] * 4, (cuuint64_t)J.fs * 4};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int t = 0; t < 2; ++t) {
+        const cuuint32_t box[4] = {(cuuint32_t)TMA_BOX_X, (cuuint32_t)(t == 0 ? 10 : 18), 1, 5};
+        for (int r = 0; r < 3; ++r)
+            if (enc(&out[3 * t + r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J.q[r], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+    }
+    return true;
+}
+
 template <typename real>
 static int create_impl(const les_grid_desc *g, const les_params *p, int njets, void *stream,
                        les_handle **out)
@@ -513,6 +557,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     h->d_stage = (double *)(B + GP.o_stage);
     h->d_fj = (FusedJet *)(B + GP.o_fj);
     h->d_oob = (unsigned long long *)(B + GP.o_oob);
+    h->d_tmap = (CUtensorMap *)(B + GP.o_tmap);
     h->d_fj1 = h->d_fj + njets;
     for (int j = 0; j < njets; ++j) {
         JetHost &J = h->J[j];
@@ -559,6 +604,18 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             F.pinf = (float)(1.0 / pp.gamma);
             for (int a = 0; a < 3; ++a) h->fj[j].h1[a] = h->J[j].h1[a];
             h->fj[j].mp = h->J[j].mp;
+            h->fj[j].tmap = nullptr;
+        }
+        // general form: TMA maps for jets whose i and j axes are not periodic
+        // (a periodic tile halo wraps, which a box cannot)
+        if (!h->sep) {
+            std::vector<CUtensorMap> maps(6 * (size_t)njets);
+            std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+            for (int j = 0; j < njets; ++j)
+                if (!h->J[j].per[0] && !h->J[j].per[1] && make_state_maps(h->J[j], &maps[6 * (size_t)j]))
+                    h->fj[j].tmap = h->d_tmap + 6 * (size_t)j;
+            CK(cudaMemcpyAsync(h->d_tmap, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                               h->st));
         }
         int rc = set_fused_tiling(h, 8, 32);
         if (rc) return bail(rc);

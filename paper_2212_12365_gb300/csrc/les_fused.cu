@@ -50,6 +50,9 @@ __constant__ float c_alpha_f[5] = {0.25f, 1.0f / 6.0f, 0.375f, 0.5f, 1.0f};
 //   SH [5][TY][FX] float  eta-interface fluxes of the current plane
 //   HX [C2X], HY [C2Y] float4  separable form: (h, 1/h, h^(2/3), 0) of the
 //                              tile's columns / rows, h = dx/dxi resp. dy/deta
+//   QG [5][C2Y][40] float       general form (in place of HX, HY, 128-byte
+//                              aligned): the next plane's state box, staged
+//                              by one TMA copy; then its mbarrier (8 bytes)
 template <int TY> struct Geo {
     static constexpr int NT = FX * TY;
     static constexpr int C2X = FX + 2, C2Y = TY + 2, NC2 = C2X * C2Y; // R2: cells [-1, FX] x [-1, TY]
@@ -67,7 +70,13 @@ template <int TY> struct Geo {
     static_assert(O_QS + 4ull * 10 * NT <= O_PB, "staging fits in MA+MB");
     static constexpr size_t O_HX = O_SH + 4ull * 5 * TY * FX;
     static constexpr size_t O_HY = O_HX + 16ull * C2X;
-    static constexpr size_t BYTES = O_HY + 16ull * C2Y;
+    static constexpr size_t BYTES_SEP = O_HY + 16ull * C2Y;
+    static constexpr size_t O_QG = (O_HX + 127) / 128 * 128;
+    static constexpr unsigned BOX_BYTES = 4u * 5 * C2Y * TMA_BOX_X;
+    static constexpr size_t O_MBAR = O_QG + BOX_BYTES;
+    static constexpr size_t BYTES_GEN = O_MBAR + 8;
+    static_assert(BOX_BYTES % 16 == 0, "box size");
+    static constexpr size_t bytes(bool sep) { return sep ? BYTES_SEP : BYTES_GEN; }
 };
 
 template <int TY> struct Sm {
@@ -75,13 +84,15 @@ template <int TY> struct Sm {
     float2 *PB, *MB;
     float *SH;
     float4 *HX, *HY;
-    float *QS;
+    float *QS, *QG;
+    unsigned long long *MBAR;
     __device__ __forceinline__ explicit Sm(unsigned char *b)
         : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
           GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
           PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH)),
           HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY)),
-          QS((float *)(b + Geo<TY>::O_QS))
+          QS((float *)(b + Geo<TY>::O_QS)), QG((float *)(b + Geo<TY>::O_QG)),
+          MBAR((unsigned long long *)(b + Geo<TY>::O_MBAR))
     {
     }
 };
@@ -117,6 +128,42 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// TMA staging of the general form: an mbarrier with one arrival (the issuing
+// thread's, carrying the expected byte count) completed by the copy.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); // visible to the copy engine
+}
+// 4-D tiled copy (x, y, z, field) of the tensor map's box into shared memory;
+// x must be a multiple of 4 elements (16 bytes); other coordinates may lie
+// outside the tensor (zero fill).
+__device__ __forceinline__ void tma_box_load(float *dst, const CUtensorMap *map, int x, int y, int z,
+                                             unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait for the phase of the given parity; bounded (false: gave up).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 
 __device__ __forceinline__ float cmp(const float4 &v, int i)
@@ -423,7 +470,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             int balanced)
 {
     using G_ = Geo<TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const Sm<TY> S(smem_raw);
     constexpr int N2 = G_::NC2, N1 = G_::NC1, C2X = G_::C2X;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -437,6 +484,15 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     // tile, then plane), cut into one column piece per tile it touches; a
     // piece starting mid-column recomputes its first zeta flux, so the result
     // does not depend on where the cuts fall.
+    // general form: the TMA staging buffer must be 128-byte aligned (the
+    // dynamic shared memory starts the window, so it is; checked anyway)
+    bool tma_smem_ok = false;
+    unsigned tpar = 0; // parity of the next staging phase
+    if constexpr (!SEP) {
+        tma_smem_ok = (smem_u32(S.QG) & 127u) == 0;
+        if (tid == 0) mbar_init(S.MBAR);
+        __syncthreads();
+    }
     int item = blockIdx.x, w = 0, wend = 0;
     if (balanced) {
         w = (int)(((long long)total_items * blockIdx.x) / gridDim.x);
@@ -519,9 +575,23 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
         }
+        // general form, no periodic i or j axis: the plane's state arrives as
+        // one TMA box [5][C2Y][40] whose x starts at the tile's first column
+        // rounded down to a multiple of 4; qg[t] is load cell t's offset in it
+        const CUtensorMap *tmap = nullptr;
+        int qg[2] = {0, 0}, tx0 = 0;
+        if constexpr (!SEP) {
+            if (F.tmap && tma_smem_ok && !pi && !pj) {
+                tmap = F.tmap + (TY == 16 ? 3 : 0) + src;
+                tx0 = (ib - 1) & ~3;
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+                    if (lc[t] >= 0) qg[t] = (lc[t] / C2X) * TMA_BOX_X + (ib - 1 - tx0) + lc[t] % C2X;
+            }
+        }
         if constexpr (SEP) {
             // 1-D spacings of the tile's columns and rows (the previous item's
-            // last reads of HX/HY precede its final barrier)
+            // last reads of HX/HY precede its closing barrier)
             if (tid < C2X) {
                 const int g = gidx(ib - 1 + tid, ni, pi);
                 S.HX[tid] = g >= 0 ? F.h1[0][g] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -557,9 +627,18 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 for (int f = 0; f < 5; ++f) cp_async4(&S.QS[(t * 5 + f) * G_::NT + tid], Qs + f * fs + o);
             }
         };
+        // general form with a tensor map: thread 0 issues the box of plane kq
+        // once every thread is done with the previous one (after a barrier)
+        auto stage_box = [&](int kq) {
+            const int gk = gidx(kq, nk, pk);
+            if (kq > k1 + 2 || gk < 0 || tid != 0) return;
+            tma_box_load(S.QG, tmap, tx0, jb - 1, gk, S.MBAR, G_::BOX_BYTES);
+        };
         if constexpr (SEP) {
             stage_q(k0 - 3);
             cp_async_commit();
+        } else {
+            if (tmap) stage_box(k0 - 3);
         }
         for (int kL = k0 - 3; kL <= k1 + 2; ++kL) {
 #pragma unroll
@@ -596,6 +675,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) qv[t][f] = 0.0f;
             if constexpr (SEP) cp_async_wait_all();
+            if (!SEP && tmap && gkL >= 0) {
+                // the box of this plane (issued one iteration earlier); a wait
+                // that gives up is recorded (site 8) instead of hanging
+                if (!mbar_wait(S.MBAR, tpar) && J.oob) atomicCAS(J.oob, 0ull, 8ull << 48);
+                tpar ^= 1u;
+            }
             if (gkL >= 0) {
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
@@ -605,8 +690,14 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
                     } else {
+                        if (tmap) {
 #pragma unroll
-                        for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
+                            for (int f = 0; f < 5; ++f)
+                                qv[t][f] = S.QG[CK_TAB(f * (G_::C2Y * TMA_BOX_X) + qg[t], 5 * G_::C2Y * TMA_BOX_X)];
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
+                        }
                     }
                 }
             }
@@ -630,6 +721,11 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
             __syncthreads();
+            // general form: the next plane's box, in flight during the rest of
+            // this iteration (every thread has read this plane's box)
+            if constexpr (!SEP) {
+                if (tmap) stage_box(kL + 1);
+            }
             // ---- derivatives, SGS, sensors, lambda-bar of plane kG on R1 (one cell per thread) ----
             if (g_act) {
                 const int s0 = CK_RING(sl[3] * N2 + c2); // plane kG
@@ -721,8 +817,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             // previous iteration's closing barrier, and the phase writes only
             // plane-kG slots, which no interface of this iteration reads.
             if constexpr (SEP) {
-                // next plane's state and the next update's Q(0), in flight
-                // during the interface arithmetic
+                // next plane's state, in flight during the interface arithmetic
                 stage_q(kL + 1);
                 cp_async_commit();
             }
@@ -868,10 +963,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 template <int TY> int fused_prepare()
 {
     int rc = (int)cudaFuncSetAttribute(k_fused<TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Geo<TY>::BYTES);
+                                       (int)Geo<TY>::BYTES_GEN);
     if (rc) return rc;
     return (int)cudaFuncSetAttribute(k_fused<TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Geo<TY>::BYTES);
+                                     (int)Geo<TY>::BYTES_SEP);
 }
 
 template <int TY>
@@ -880,10 +975,10 @@ void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int 
 {
     dim3 block(FX, TY);
     if (separable)
-        k_fused<TY, true><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
+        k_fused<TY, true><<<grid, block, Geo<TY>::BYTES_SEP, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
                                                               rhs_only, balanced);
     else
-        k_fused<TY, false><<<grid, block, Geo<TY>::BYTES, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
+        k_fused<TY, false><<<grid, block, Geo<TY>::BYTES_GEN, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
                                                                rhs_only, balanced);
 }
 

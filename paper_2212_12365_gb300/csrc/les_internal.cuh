@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h> // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "les.h"
@@ -253,7 +254,16 @@ struct FusedJet {
     // general form: the static fields of each point packed as four float4
     // records (m0..m3 | m4..m7 | m8, J^-1, (Cs Delta)^2, J | row norms, 0)
     const float4 *mp;
+    // general form, jets with no periodic i or j axis: tensor maps of the
+    // three state registers for the TMA staging of the next plane (null:
+    // plain loads)
+    const CUtensorMap *tmap;
 };
+
+// TMA staging box of the fused stage: 5 fields x 1 plane x (TY + 2) rows x
+// 40 columns (the tile's 34 columns plus up to 3 for aligning the start
+// column down to a multiple of 4, i.e. 16 bytes).
+constexpr int TMA_BOX_X = 40;
 
 template <int TY> int fused_prepare();
 template <int TY>
