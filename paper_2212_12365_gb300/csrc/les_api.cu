@@ -606,9 +606,9 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             h->fj[j].mp = h->J[j].mp;
             h->fj[j].tmap = nullptr;
         }
-        // general form: TMA maps for jets whose i and j axes are not periodic
-        // (a periodic tile halo wraps, which a box cannot)
-        if (!h->sep) {
+        // TMA maps for jets whose i and j axes are not periodic (a periodic
+        // tile halo wraps, which a box cannot)
+        {
             std::vector<CUtensorMap> maps(6 * (size_t)njets);
             std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
             for (int j = 0; j < njets; ++j)

@@ -71,11 +71,16 @@ template <int TY> struct Geo {
     static constexpr size_t O_HX = O_SH + 4ull * 5 * TY * FX;
     static constexpr size_t O_HY = O_HX + 16ull * C2X;
     static constexpr size_t BYTES_SEP = O_HY + 16ull * C2Y;
-    static constexpr size_t O_QG = (O_HX + 127) / 128 * 128;
     static constexpr unsigned BOX_BYTES = 4u * 5 * C2Y * TMA_BOX_X;
+    static_assert(BOX_BYTES % 16 == 0, "box size");
+    // TMA box and its mbarrier: after the eta-flux rows (general form), or
+    // in the metric-table region the separable form does not use
+    static constexpr size_t O_QG = (O_HX + 127) / 128 * 128;
     static constexpr size_t O_MBAR = O_QG + BOX_BYTES;
     static constexpr size_t BYTES_GEN = O_MBAR + 8;
-    static_assert(BOX_BYTES % 16 == 0, "box size");
+    static constexpr size_t O_QG_SEP = (O_MA + 127) / 128 * 128;
+    static constexpr size_t O_MBAR_SEP = O_QG_SEP + BOX_BYTES;
+    static_assert(O_MBAR_SEP + 8 <= O_PB, "separable form: box fits in the metric-table region");
     static constexpr size_t bytes(bool sep) { return sep ? BYTES_SEP : BYTES_GEN; }
 };
 
@@ -86,13 +91,13 @@ template <int TY> struct Sm {
     float4 *HX, *HY;
     float *QS, *QG;
     unsigned long long *MBAR;
-    __device__ __forceinline__ explicit Sm(unsigned char *b)
+    __device__ __forceinline__ Sm(unsigned char *b, bool sep)
         : PA((float4 *)(b + Geo<TY>::O_PA)), GD((float4 *)(b + Geo<TY>::O_GD)),
           GC((float4 *)(b + Geo<TY>::O_GC)), MA((float4 *)(b + Geo<TY>::O_MA)),
           PB((float2 *)(b + Geo<TY>::O_PB)), MB((float2 *)(b + Geo<TY>::O_MB)), SH((float *)(b + Geo<TY>::O_SH)),
           HX((float4 *)(b + Geo<TY>::O_HX)), HY((float4 *)(b + Geo<TY>::O_HY)),
-          QS((float *)(b + Geo<TY>::O_QS)), QG((float *)(b + Geo<TY>::O_QG)),
-          MBAR((unsigned long long *)(b + Geo<TY>::O_MBAR))
+          QS((float *)(b + Geo<TY>::O_QS)), QG((float *)(b + (sep ? Geo<TY>::O_QG_SEP : Geo<TY>::O_QG))),
+          MBAR((unsigned long long *)(b + (sep ? Geo<TY>::O_MBAR_SEP : Geo<TY>::O_MBAR)))
     {
     }
 };
@@ -471,7 +476,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 {
     using G_ = Geo<TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Sm<TY> S(smem_raw);
+    const Sm<TY> S(smem_raw, SEP);
     constexpr int N2 = G_::NC2, N1 = G_::NC1, C2X = G_::C2X;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
@@ -486,13 +491,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     // does not depend on where the cuts fall.
     // general form: the TMA staging buffer must be 128-byte aligned (the
     // dynamic shared memory starts the window, so it is; checked anyway)
-    bool tma_smem_ok = false;
+    const bool tma_smem_ok = (smem_u32(S.QG) & 127u) == 0;
     unsigned tpar = 0; // parity of the next staging phase
-    if constexpr (!SEP) {
-        tma_smem_ok = (smem_u32(S.QG) & 127u) == 0;
-        if (tid == 0) mbar_init(S.MBAR);
-        __syncthreads();
-    }
+    if (tid == 0) mbar_init(S.MBAR);
+    __syncthreads();
     int item = blockIdx.x, w = 0, wend = 0;
     if (balanced) {
         w = (int)(((long long)total_items * blockIdx.x) / gridDim.x);
@@ -575,19 +577,17 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
         }
-        // general form, no periodic i or j axis: the plane's state arrives as
-        // one TMA box [5][C2Y][40] whose x starts at the tile's first column
+        // jets with no periodic i or j axis: the plane's state arrives as one
+        // TMA box [5][C2Y][40] whose x starts at the tile's first column
         // rounded down to a multiple of 4; qg[t] is load cell t's offset in it
         const CUtensorMap *tmap = nullptr;
         int qg[2] = {0, 0}, tx0 = 0;
-        if constexpr (!SEP) {
-            if (F.tmap && tma_smem_ok && !pi && !pj) {
-                tmap = F.tmap + (TY == 16 ? 3 : 0) + src;
-                tx0 = (ib - 1) & ~3;
+        if (F.tmap && tma_smem_ok && !pi && !pj) {
+            tmap = F.tmap + (TY == 16 ? 3 : 0) + src;
+            tx0 = (ib - 1) & ~3;
 #pragma unroll
-                for (int t = 0; t < 2; ++t)
-                    if (lc[t] >= 0) qg[t] = (lc[t] / C2X) * TMA_BOX_X + (ib - 1 - tx0) + lc[t] % C2X;
-            }
+            for (int t = 0; t < 2; ++t)
+                if (lc[t] >= 0) qg[t] = (lc[t] / C2X) * TMA_BOX_X + (ib - 1 - tx0) + lc[t] % C2X;
         }
         if constexpr (SEP) {
             // 1-D spacings of the tile's columns and rows (the previous item's
@@ -612,10 +612,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         // state is stored unscaled, so the update is Q(l) = Q(0) - alpha dt J R)
         float rjU = 0.0f;
         __syncthreads(); // shared memory of the previous item is free
-        // separable form: the state of plane kq at this thread's load cells is
-        // staged in shared memory one iteration ahead by asynchronous copies,
-        // so the load phase finds it there; each thread reads only what it
-        // copied
+        // separable form without a tensor map: the state of plane kq at this
+        // thread's load cells is staged in shared memory one iteration ahead by
+        // asynchronous copies, so the load phase finds it there; each thread
+        // reads only what it copied
         auto stage_q = [&](int kq) {
             const int gk = gidx(kq, nk, pk);
             if (kq > k1 + 2 || gk < 0) return;
@@ -627,18 +627,18 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 for (int f = 0; f < 5; ++f) cp_async4(&S.QS[(t * 5 + f) * G_::NT + tid], Qs + f * fs + o);
             }
         };
-        // general form with a tensor map: thread 0 issues the box of plane kq
-        // once every thread is done with the previous one (after a barrier)
+        // with a tensor map: thread 0 issues the box of plane kq once every
+        // thread is done with the previous one (after a barrier)
         auto stage_box = [&](int kq) {
             const int gk = gidx(kq, nk, pk);
             if (kq > k1 + 2 || gk < 0 || tid != 0) return;
             tma_box_load(S.QG, tmap, tx0, jb - 1, gk, S.MBAR, G_::BOX_BYTES);
         };
-        if constexpr (SEP) {
+        if (tmap) {
+            stage_box(k0 - 3);
+        } else if constexpr (SEP) {
             stage_q(k0 - 3);
             cp_async_commit();
-        } else {
-            if (tmap) stage_box(k0 - 3);
         }
         for (int kL = k0 - 3; kL <= k1 + 2; ++kL) {
 #pragma unroll
@@ -674,8 +674,8 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) qv[t][f] = 0.0f;
-            if constexpr (SEP) cp_async_wait_all();
-            if (!SEP && tmap && gkL >= 0) {
+            if (SEP && !tmap) cp_async_wait_all();
+            if (tmap && gkL >= 0) {
                 // the box of this plane (issued one iteration earlier); a wait
                 // that gives up is recorded (site 8) instead of hanging
                 if (!mbar_wait(S.MBAR, tpar) && J.oob) atomicCAS(J.oob, 0ull, 8ull << 48);
@@ -686,18 +686,16 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
                     const long long o = CK_G(2, gkL * plane + lo2[t]);
-                    if constexpr (SEP) {
+                    if (tmap) {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f)
+                            qv[t][f] = S.QG[CK_TAB(f * (G_::C2Y * TMA_BOX_X) + qg[t], 5 * G_::C2Y * TMA_BOX_X)];
+                    } else if constexpr (SEP) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
                     } else {
-                        if (tmap) {
 #pragma unroll
-                            for (int f = 0; f < 5; ++f)
-                                qv[t][f] = S.QG[CK_TAB(f * (G_::C2Y * TMA_BOX_X) + qg[t], 5 * G_::C2Y * TMA_BOX_X)];
-                        } else {
-#pragma unroll
-                            for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
-                        }
+                        for (int f = 0; f < 5; ++f) qv[t][f] = Qs[f * fs + o];
                     }
                 }
             }
@@ -721,11 +719,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                 }
             }
             __syncthreads();
-            // general form: the next plane's box, in flight during the rest of
-            // this iteration (every thread has read this plane's box)
-            if constexpr (!SEP) {
-                if (tmap) stage_box(kL + 1);
-            }
+            // the next plane's box, in flight during the rest of this iteration
+            // (every thread has read this plane's box)
+            if (tmap) stage_box(kL + 1);
             // ---- derivatives, SGS, sensors, lambda-bar of plane kG on R1 (one cell per thread) ----
             if (g_act) {
                 const int s0 = CK_RING(sl[3] * N2 + c2); // plane kG
@@ -816,7 +812,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             // threads (plane kU tables, the point ring) was written before the
             // previous iteration's closing barrier, and the phase writes only
             // plane-kG slots, which no interface of this iteration reads.
-            if constexpr (SEP) {
+            if (SEP && !tmap) {
                 // next plane's state, in flight during the interface arithmetic
                 stage_q(kL + 1);
                 cp_async_commit();
