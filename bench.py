@@ -40,12 +40,12 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
                            "fp32-sep": 14 * 4}
 # DRAM bytes per point of one launch of the dominant kernel, from the ncu
 # captures summarised in profiles/ (None once the kernel changed since).
-TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 95.6}
+TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 95.8}
 # Arithmetic-pipe utilisation of the dominant kernel from the same committed
 # ncu captures (sm__inst_executed_pipe_*, % of peak sustained while active)
 PIPE_UTIL_NCU = {("fp64", "k_iface"): {"sm__inst_executed_pipe_fp64": 0.872},
-                 ("fp32", "k_fused"): {"sm__inst_executed_pipe_fma": 0.287, "sm__inst_executed_pipe_alu": 0.237,
-                                       "smsp__issue_active": 0.503}}
+                 ("fp32", "k_fused"): {"sm__inst_executed_pipe_fma": 0.292, "sm__inst_executed_pipe_alu": 0.253,
+                                       "smsp__issue_active": 0.528}}
 # Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
