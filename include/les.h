@@ -47,7 +47,7 @@ extern "C" {
 #define LES_ERR_OOM (-2)       /* device allocation failed / workspace too small */
 #define LES_ERR_CUDA (-3)      /* a CUDA runtime call failed */
 #define LES_ERR_NONFINITE (-4) /* diagnostics found NaN/Inf in the state or residual */
-#define LES_ERR_TIMEOUT (-5)   /* reserved: no device-side wait exists in this library */
+#define LES_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up (fused FP32 stage staging copy) */
 #define LES_ERR_STATE (-6)     /* call out of order (e.g. step before set_state) */
 
 /* Face boundary conditions (Sec. "Boundary Conditions").  Faces are ordered
@@ -175,7 +175,13 @@ int les_set_state_jet(les_handle *h, int jet, const double *q, int kind);
 int les_step(les_handle *h, int nsteps);
 
 /* Copy the state of jet 0 / jet `jet` to the host array q (5*N, `kind`).
- * Synchronises the stream. */
+ * Synchronises the stream.  Errors: LES_ERR_ARG, LES_ERR_CUDA, and, for FP32
+ * handles, LES_ERR_TIMEOUT once a staging wait of the fused stage (the
+ * bounded wait for the TMA copy of the next plane's state) has given up since
+ * the handle was created.  The stage then reads that plane, and every later
+ * one of the launch, directly from global memory, so q is still written and
+ * holds the state a normal step gives; the handle keeps reporting the
+ * timeout (it points to a stalled copy engine). */
 int les_get_state(les_handle *h, double *q, int kind);
 int les_get_state_jet(les_handle *h, int jet, double *q, int kind);
 
@@ -202,7 +208,8 @@ int les_probe_frames(les_handle *h, int64_t *frames);
 /* Residual monitor of jet 0 / jet `jet` (Sec. "Computational Performance
  * Assessment": max |RHS| of continuity) and conservation sums, computed from
  * the current state.  Returns LES_ERR_NONFINITE if any state or residual
- * value is NaN/Inf (d is still filled).  Synchronises the stream. */
+ * value is NaN/Inf, LES_ERR_TIMEOUT as les_get_state does (d is still filled
+ * in both cases).  Synchronises the stream. */
 int les_get_diagnostics(les_handle *h, les_diag *d);
 int les_get_diagnostics_jet(les_handle *h, int jet, les_diag *d);
 
@@ -236,6 +243,15 @@ int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts)
  * (FP64 handle, bad ty or kc). */
 int les_set_fused_tiling(les_handle *h, int ty, int kc);
 
+/* Test access to the timeout path of the fused FP32 stage: max_polls >= 0
+ * bounds every staging wait to that many polls of its mbarrier (0: the first
+ * wait of each CTA gives up at once, while its copy is still in flight, so
+ * that the fallback to direct loads and the LES_ERR_TIMEOUT report run on a
+ * healthy device); -1 restores the default (2^22 polls).  The copy a wait
+ * gave up on is still waited for, with the default bound, before the CTA
+ * exits.  Errors: LES_ERR_ARG (FP64 handle, max_polls < -1). */
+int les_debug_stage_wait(les_handle *h, int max_polls);
+
 /* Kernel launches issued by the most recent les_step call (all steps). */
 int64_t les_last_launch_count(les_handle *h);
 
@@ -251,8 +267,10 @@ int64_t les_last_launch_count(les_handle *h);
  * for handle h since its creation: 0 if none, else (site << 48) | value with
  * site 1 a point index (value = k << 32 | j << 16 | i, 16 bits each), 2-4 a
  * fused-stage global offset (state, static record, update), 5-7 a fused-stage
- * shared-memory slot (point ring, plane tables, eta-flux rows); always 0 in a
- * normal build.  Synchronises the stream.  Errors: LES_ERR_ARG. */
+ * shared-memory slot (point ring, plane tables, eta-flux rows).  In every
+ * build, site 8 records a staging wait of the fused stage that gave up (see
+ * les_get_state); in a normal build no other site is recorded.
+ * Synchronises the stream.  Errors: LES_ERR_ARG. */
 int les_bounds_checking(void);
 int les_bounds_violation(les_handle *h, uint64_t *out);
 

@@ -69,7 +69,10 @@ struct les_handle {
     double *d_diag = nullptr;
     long long *d_probe_base = nullptr;
     double *d_stage = nullptr;   // 5*max(N) doubles: host transfer staging
-    unsigned long long *d_oob = nullptr; // first out-of-range index (bounds-checked builds)
+    // error word: the first out-of-range index (bounds-checked builds) or a
+    // staging wait of the fused stage that gave up (site 8, every build)
+    unsigned long long *d_oob = nullptr;
+    int stage_wait_limit = -1; // polls per staging wait of the fused stage (-1: the default)
     CUtensorMap *d_tmap = nullptr; // per jet: TMA maps of the 3 state registers for TY 8 and 16
     int nblk_diag = 0;
     int64_t step = 0;
@@ -112,6 +115,23 @@ static int fail(les_handle *h, int code, const std::string &msg)
 {
     if (h) h->err = msg;
     return code;
+}
+
+// Status of the fused FP32 stage's bounded staging waits (call after a stream
+// synchronisation): LES_ERR_TIMEOUT once a wait has given up (site 8 in the
+// handle's error word; the word is not cleared, so the handle keeps
+// reporting it).  The stage then read its input from global memory, so the
+// results are those of a normal step.
+static int wait_status(les_handle *h)
+{
+    if (h->prec != LES_FP32) return LES_OK;
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_oob, sizeof(v), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if ((v >> 48) == 8)
+        return fail(h, LES_ERR_TIMEOUT,
+                    "a staging wait of the fused stage gave up (the stage fell back to direct loads)");
+    return LES_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -434,9 +454,11 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     if (jet >= 0) jets += jet;
     const int bal = h->fused_balanced ? 1 : 0;
     if (h->fused_ty == 16)
-        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal, st);
+        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
+                         h->stage_wait_limit, st);
     else
-        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal, st);
+        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
+                         h->stage_wait_limit, st);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the
@@ -983,7 +1005,7 @@ template <typename real> static int get_state_impl(les_handle *h, int jet, doubl
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(q, h->d_stage, (size_t)J.N * 5 * 8, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    return LES_OK;
+    return wait_status(h);
 }
 
 extern "C" int les_get_state_jet(les_handle *h, int jet, double *q, int kind)
@@ -1118,6 +1140,7 @@ template <typename real> static int diag_impl(les_handle *h, int jet, les_diag *
         d->sum_qhat[f] = out[6 + f];
     }
     d->nonfinite = (int64_t)out[11];
+    if (int rc = wait_status(h)) return rc;
     if (d->nonfinite > 0 || !std::isfinite(out[0])) return fail(h, LES_ERR_NONFINITE, "non-finite values in state or residual");
     return LES_OK;
 }
@@ -1181,6 +1204,19 @@ extern "C" int les_debug_field(les_handle *h, int jet, int field, double *out)
         rc = export_impl<float>(h, jet, field, out, N);
     }
     return rc;
+}
+
+extern "C" int les_debug_stage_wait(les_handle *h, int max_polls)
+{
+    if (!h) return LES_ERR_ARG;
+    if (h->prec != LES_FP32) return fail(h, LES_ERR_ARG, "staging waits exist in FP32 handles only");
+    if (max_polls < -1) return fail(h, LES_ERR_ARG, "max_polls must be >= 0, or -1 for the default");
+    h->stage_wait_limit = max_polls;
+    if (h->gexec) { // the captured step holds the old launch parameters
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return LES_OK;
 }
 
 // ---------------------------------------------------------------------------

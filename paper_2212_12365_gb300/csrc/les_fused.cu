@@ -155,10 +155,12 @@ __device__ __forceinline__ void tma_box_load(float *dst, const CUtensorMap *map,
                  "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
                  : "memory");
 }
-// Wait for the phase of the given parity; bounded (false: gave up).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// Wait for the phase of the given parity, polling at most `limit` times
+// (false: gave up).
+constexpr int MBAR_WAIT_LIMIT = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int limit)
 {
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -472,7 +474,7 @@ template <int TY, bool SEP>
 __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
             int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only,
-            int balanced)
+            int balanced, int wait_limit)
 {
     using G_ = Geo<TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -493,6 +495,12 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     // dynamic shared memory starts the window, so it is; checked anyway)
     const bool tma_smem_ok = (smem_u32(S.QG) & 127u) == 0;
     unsigned tpar = 0; // parity of the next staging phase
+    // A staging wait that gives up (wait_limit polls) is recorded in the
+    // jet's error word (site 8); from the next barrier on the whole CTA reads
+    // the state directly from global memory for the rest of the launch, and
+    // thread 0, which issued the outstanding copy, waits for it (bounded)
+    // before the CTA exits.
+    bool tma_off = false, pend = false;
     if (tid == 0) mbar_init(S.MBAR);
     __syncthreads();
     int item = blockIdx.x, w = 0, wend = 0;
@@ -582,7 +590,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         // rounded down to a multiple of 4; qg[t] is load cell t's offset in it
         const CUtensorMap *tmap = nullptr;
         int qg[2] = {0, 0}, tx0 = 0;
-        if (F.tmap && tma_smem_ok && !pi && !pj) {
+        if (F.tmap && tma_smem_ok && !pi && !pj && !tma_off) {
             tmap = F.tmap + (TY == 16 ? 3 : 0) + src;
             tx0 = (ib - 1) & ~3;
 #pragma unroll
@@ -636,7 +644,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         };
         if (tmap) {
             stage_box(k0 - 3);
-        } else if constexpr (SEP) {
+        } else if (SEP && !tma_off) {
             stage_q(k0 - 3);
             cp_async_commit();
         }
@@ -675,22 +683,30 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) qv[t][f] = 0.0f;
             if (SEP && !tmap) cp_async_wait_all();
+            bool from_box = false;
             if (tmap && gkL >= 0) {
                 // the box of this plane (issued one iteration earlier); a wait
-                // that gives up is recorded (site 8) instead of hanging
-                if (!mbar_wait(S.MBAR, tpar) && J.oob) atomicCAS(J.oob, 0ull, 8ull << 48);
-                tpar ^= 1u;
+                // that gives up is recorded (site 8) instead of hanging, and
+                // this thread reads the plane from global memory
+                if (mbar_wait(S.MBAR, tpar, wait_limit)) {
+                    from_box = true;
+                    tpar ^= 1u;
+                } else {
+                    if (J.oob) atomicCAS(J.oob, 0ull, 8ull << 48);
+                    tma_off = true;
+                    pend = true;
+                }
             }
             if (gkL >= 0) {
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
                     const long long o = CK_G(2, gkL * plane + lo2[t]);
-                    if (tmap) {
+                    if (from_box) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f)
                             qv[t][f] = S.QG[CK_TAB(f * (G_::C2Y * TMA_BOX_X) + qg[t], 5 * G_::C2Y * TMA_BOX_X)];
-                    } else if constexpr (SEP) {
+                    } else if (SEP && !tmap && !tma_off) {
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qv[t][f] = S.QS[(t * 5 + f) * G_::NT + tid];
                     } else {
@@ -718,7 +734,10 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
                     S.PB[CK_RING(sb + lc[t])] = make_float2(p, FP.gam * p * rr);
                 }
             }
-            __syncthreads();
+            // (a thread whose staging wait gave up turns staging off for the
+            // whole CTA here)
+            tma_off = __syncthreads_or(tma_off) != 0;
+            if (tma_off) tmap = nullptr;
             // the next plane's box, in flight during the rest of this iteration
             // (every thread has read this plane's box)
             if (tmap) stage_box(kL + 1);
@@ -812,7 +831,7 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             // threads (plane kU tables, the point ring) was written before the
             // previous iteration's closing barrier, and the phase writes only
             // plane-kG slots, which no interface of this iteration reads.
-            if (SEP && !tmap) {
+            if (SEP && !tmap && !tma_off) {
                 // next plane's state, in flight during the interface arithmetic
                 stage_q(kL + 1);
                 cp_async_commit();
@@ -949,6 +968,9 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
             __syncthreads();
         }
     }
+    // a copy whose wait gave up may still be in flight into this CTA's
+    // shared memory: its issuer waits for it (bounded) before exiting
+    if (pend && tid == 0) mbar_wait(S.MBAR, tpar, MBAR_WAIT_LIMIT);
 }
 
 #undef CK_G
@@ -967,22 +989,24 @@ template <int TY> int fused_prepare()
 
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid, int src,
-                  int dst, int stage, const double *dt, int rhs_only, int separable, int balanced, cudaStream_t st)
+                  int dst, int stage, const double *dt, int rhs_only, int separable, int balanced, int wait_limit,
+                  cudaStream_t st)
 {
     dim3 block(FX, TY);
+    if (wait_limit < 0) wait_limit = MBAR_WAIT_LIMIT;
     if (separable)
         k_fused<TY, true><<<grid, block, Geo<TY>::BYTES_SEP, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                              rhs_only, balanced);
+                                                              rhs_only, balanced, wait_limit);
     else
         k_fused<TY, false><<<grid, block, Geo<TY>::BYTES_GEN, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                               rhs_only, balanced);
+                                                               rhs_only, balanced, wait_limit);
 }
 
 template int fused_prepare<16>();
 template int fused_prepare<8>();
 template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                               const double *, int, int, int, cudaStream_t);
+                               const double *, int, int, int, int, cudaStream_t);
 template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
-                              const double *, int, int, int, cudaStream_t);
+                              const double *, int, int, int, int, cudaStream_t);
 
 } // namespace les

@@ -269,7 +269,7 @@ template <int TY> int fused_prepare();
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
                   int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
-                  cudaStream_t st);
+                  int wait_limit, cudaStream_t st);
 
 // Separable form: 1-D spacings of a Cartesian-product grid from device
 // coordinates (FP64 derivative stencils of the metric computation).

@@ -34,7 +34,7 @@ EXPORTED = [
     "les_set_state_jet", "les_step", "les_get_state", "les_get_state_jet", "les_set_time",
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
-    "les_set_fused_tiling", "les_last_launch_count", "les_bounds_checking", "les_bounds_violation",
+    "les_set_fused_tiling", "les_debug_stage_wait", "les_last_launch_count", "les_bounds_checking", "les_bounds_violation",
     "les_diag_sums_noalloc", "les_describe",
     "les_last_error", "les_destroy",
 ]
@@ -97,6 +97,7 @@ def lib():
         L.les_debug_field.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp]
         L.les_profile_step.argtypes = [vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]
         L.les_set_fused_tiling.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.les_debug_stage_wait.argtypes = [vp, ctypes.c_int]
         L.les_last_launch_count.argtypes = [vp]
         L.les_last_launch_count.restype = ctypes.c_int64
         L.les_bounds_checking.argtypes = []
@@ -225,7 +226,7 @@ def les_get_time(h):
 def les_get_diagnostics(h, jet: int = 0, check: bool = True) -> dict:
     d = les_diag()
     rc = lib().les_get_diagnostics_jet(h, jet, ctypes.byref(d))
-    if check or rc not in (LES_OK, LES_ERR_NONFINITE):
+    if check or rc not in (LES_OK, LES_ERR_NONFINITE, LES_ERR_TIMEOUT):
         _check(h, rc)
     return {"dt": d.dt, "step": d.step, "max_abs_rhs_rho": d.max_abs_rhs_rho,
             "l2_rhs": np.array(d.l2_rhs[:]), "sum_qhat": np.array(d.sum_qhat[:]),
@@ -277,6 +278,18 @@ def les_set_fused_tiling(h, ty: int, kc: int):
     _check(h, lib().les_set_fused_tiling(h, int(ty), int(kc)))
 
 
+def les_debug_stage_wait(h, max_polls: int):
+    """Bound the fused FP32 stage's staging waits to max_polls polls (-1: default)."""
+    _check(h, lib().les_debug_stage_wait(h, int(max_polls)))
+
+
+def les_get_state_rc(h, n_points: int, kind: int, jet: int = 0):
+    """The state and the return code of les_get_state_jet, without raising."""
+    out = np.empty((5, n_points))
+    rc = lib().les_get_state_jet(h, jet, _dptr(out), kind)
+    return out, rc
+
+
 def les_last_launch_count(h) -> int:
     return int(lib().les_last_launch_count(h))
 
@@ -288,7 +301,8 @@ def les_bounds_checking() -> bool:
 
 def les_bounds_violation(h) -> int:
     """First out-of-range index met by the handle's kernels ((site << 48) |
-    value), 0 if none (always 0 in a normal build)."""
+    value), 0 if none; site 8 (any build) is a staging wait of the fused
+    FP32 stage that gave up."""
     v = ctypes.c_uint64(0)
     _check(h, lib().les_bounds_violation(h, ctypes.byref(v)))
     return int(v.value)

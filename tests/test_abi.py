@@ -55,6 +55,11 @@ def test_bounds_checked_build_loads_and_reports_itself(lib):
     assert lib.les_bounds_violation(None, ctypes.byref(out)) != 0  # NULL handle: LES_ERR_ARG
 
 
+def test_stage_wait_bound_rejects_null_handle(lib):
+    from paper_2212_12365_gb300 import les
+    assert lib.les_debug_stage_wait(None, 0) == les.LES_ERR_ARG
+
+
 def _desc(spec, **over):
     from paper_2212_12365_gb300 import les
     keep = []
