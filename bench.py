@@ -17,6 +17,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -38,9 +39,15 @@ FLOPS_PER_PT_STAGE = {"point": 96, "grads": 141, "iface": 765, "update": 41}
 ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
                            # separable metrics (product grids): no 3-D metric fields, 14 values
                            "fp32-sep": 14 * 4}
-# DRAM bytes per point of one launch of the dominant kernel, from the ncu
-# captures summarised in profiles/ (None once the kernel changed since).
-TRAFFIC_BYTES_PER_POINT = {("fp64", "k_iface"): 938.0, ("fp32", "k_fused"): 95.8}
+# DRAM bytes per point of one launch of the dominant kernel in the launch
+# configuration of the run, from the ncu captures summarised in profiles/:
+# keyed by workload, precision, kernel and (fused stage) the decomposition in
+# use; the paper-scale FP32 figures are those of the decomposition the tuner
+# picks there (32 x 8 tiles, balanced tile-plane ranges).  None for anything
+# not captured, and once the kernel has changed since the capture.
+TRAFFIC_BYTES_PER_POINT = {("jet-384x256x144", "fp64", "k_iface", None): 938.0,
+                           ("jet-384x256x144", "fp32", "k_fused", "ty=8 kc=balanced"): 196.8,
+                           ("jet-384x256x144", "fp32-sep", "k_fused", "ty=8 kc=balanced"): 94.2}
 # Arithmetic-pipe utilisation of the dominant kernel from the same committed
 # ncu captures (sm__inst_executed_pipe_*, % of peak sustained while active)
 PIPE_UTIL_NCU = {("fp64", "k_iface"): {"sm__inst_executed_pipe_fp64": 0.872},
@@ -378,7 +385,11 @@ def run_ours(args):
     achieved = flops_pt * N / t_launch / 1e12
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6750.0)
-    traffic_pt = TRAFFIC_BYTES_PER_POINT.get((prec, kname))
+    decomp = None
+    if prec != "fp64":
+        mt = re.search(r"ty=(\d+) kc=(\w+)", les.les_describe(solver.h))
+        decomp = f"ty={mt.group(1)} kc={mt.group(2)}" if mt else None
+    traffic_pt = TRAFFIC_BYTES_PER_POINT.get((args.workload, prec, kname, decomp))
     bytes_pt_stage = ALGO_BYTES_PER_PT_STAGE[prec]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_pt * N if traffic_pt else None,
