@@ -421,9 +421,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(ke):
-            les.lib().les_set_state_jet(solver.h, 0, les._dptr(host_in.numpy()), les.LES_STATE_RAW)
+            les._check(solver.h, les.lib().les_set_state_jet(solver.h, 0, les._dptr(host_in.numpy()),
+                                                             les.LES_STATE_RAW))
             solver.step(1)
-            les.lib().les_get_state_jet(solver.h, 0, les._dptr(host_out.numpy()), les.LES_STATE_RAW)
+            les._check(solver.h, les.lib().les_get_state_jet(solver.h, 0, les._dptr(host_out.numpy()),
+                                                             les.LES_STATE_RAW))
         ev1.record(stream)
         torch.cuda.synchronize()
         ems = ev0.elapsed_time(ev1)
