@@ -42,12 +42,17 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
 # DRAM bytes per point of one launch of the dominant kernel in the launch
 # configuration of the run, from the ncu captures summarised in profiles/:
 # keyed by workload, precision, kernel and (fused stage) the decomposition in
-# use; the paper-scale FP32 figures are those of the decomposition the tuner
-# picks there (32 x 8 tiles, balanced tile-plane ranges).  None for anything
-# not captured, and once the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_POINT = {("jet-384x256x144", "fp64", "k_iface", None): 938.0,
-                           ("jet-384x256x144", "fp32", "k_fused", "ty=8 kc=balanced"): 196.8,
-                           ("jet-384x256x144", "fp32-sep", "k_fused", "ty=8 kc=balanced"): 94.2}
+# use (the tuner's pick on the paper-scale jet is one of those listed).  None
+# for anything not captured, and once the kernel has changed since the
+# capture.
+_PAPER_JET = "jet-384x256x144"
+TRAFFIC_BYTES_PER_POINT = {(_PAPER_JET, "fp64", "k_iface", None): 938.0,
+                           (_PAPER_JET, "fp32", "k_fused", "ty=8 kc=lockstep"): 148.3,
+                           (_PAPER_JET, "fp32", "k_fused", "ty=8 kc=balanced"): 196.7,
+                           (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): 128.1,
+                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=lockstep"): 63.9,
+                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=balanced"): 93.9,
+                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): 54.0}
 # Arithmetic-pipe utilisation of the dominant kernel from the same committed
 # ncu captures (sm__inst_executed_pipe_*, % of peak sustained while active)
 PIPE_UTIL_NCU = {("fp64", "k_iface"): {"sm__inst_executed_pipe_fp64": 0.872},

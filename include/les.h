@@ -235,12 +235,15 @@ int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts)
 
 /* Work decomposition of the fused FP32 stage (LES_FP32, LES_FP32_SEPARABLE
  * handles): ty = 8 or 16 grid rows per CTA tile (32 x ty threads), kc >= 1
- * planes per k-chunk item, or kc = 0 for the balanced form (every CTA of the
- * persistent grid takes one contiguous, equal share of all tile-planes).  By
- * default the first les_step picks the fastest choice by timing them
- * (autotuner); this call sets it instead and disables the tuning for the
- * handle.  Results are bit-identical for every choice.  Errors: LES_ERR_ARG
- * (FP64 handle, bad ty or kc). */
+ * planes per k-chunk item, kc = 0 for the balanced form (every CTA of the
+ * persistent grid takes one contiguous, equal share of all tile-planes), or
+ * kc = -1 for the lockstep form (whole columns in waves of one tile per CTA,
+ * so that neighbouring tiles share their halo planes through L2, then the
+ * remaining tile-planes shared out as in the balanced form).  By default the
+ * first les_step picks the fastest choice by timing them (autotuner); this
+ * call sets it instead and disables the tuning for the handle.  Results are
+ * bit-identical for every choice.  Errors: LES_ERR_ARG (FP64 handle, bad ty,
+ * kc < -1). */
 int les_set_fused_tiling(les_handle *h, int ty, int kc);
 
 /* Test access to the timeout path of the fused FP32 stage: max_polls >= 0

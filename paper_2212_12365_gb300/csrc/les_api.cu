@@ -83,8 +83,8 @@ struct les_handle {
     FusedJet *d_fj = nullptr, *d_fj1 = nullptr;
     std::vector<FusedJet> fj;
     int fused_ty = 16;
-    bool fused_balanced = false;
-    int fused_items = 0;
+    int fused_balanced = 0; // 0: k-chunk items, 1: balanced ranges, 2: lockstep waves, then balanced ranges
+    int fused_items = 0, fused_tiles = 0;
     bool tuned = false;
     std::string tune_note;
     int64_t launches_per_step = 0;
@@ -409,17 +409,18 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
 static int out_len(const JetHost &J, int a) { return J.per[a] ? J.n[a] : J.n[a] - 2; }
 
 // Work-list tables of the fused stage for tile height ty and k-chunk kc
-// (kc = 0: balanced form, items are tile-planes split evenly over the grid).
+// (kc = 0: balanced form, items are tile-planes split evenly over the grid;
+// kc = -1: the same after waves of whole columns, in lockstep).
 static int set_fused_tiling(les_handle *h, int ty, int kc)
 {
-    int acc = 0;
+    int acc = 0, tiles = 0;
     std::vector<FusedJet> one(h->njets);
     for (int j = 0; j < h->njets; ++j) {
         FusedJet &F = h->fj[j];
         const JetHost &J = h->J[j];
         F.nbx = (out_len(J, 0) + 29) / 30;
         F.nby = (out_len(J, 1) + ty - 3) / (ty - 2);
-        if (kc == 0) {
+        if (kc <= 0) {
             F.kc = 0;
             F.nkc = out_len(J, 2); // planes per column: the items are tile-planes
         } else {
@@ -427,13 +428,17 @@ static int set_fused_tiling(les_handle *h, int ty, int kc)
             F.nkc = (out_len(J, 2) + F.kc - 1) / F.kc;
         }
         F.item0 = acc;
+        F.tile0 = tiles;
         acc += F.nbx * F.nby * F.nkc;
+        tiles += F.nbx * F.nby;
         one[j] = F;
         one[j].item0 = 0;
+        one[j].tile0 = 0;
     }
     h->fused_ty = ty;
-    h->fused_balanced = kc == 0;
+    h->fused_balanced = kc == 0 ? 1 : (kc < 0 ? 2 : 0);
     h->fused_items = acc;
+    h->fused_tiles = tiles;
     CK(cudaMemcpyAsync(h->d_fj, h->fj.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_fj1, one.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -441,6 +446,10 @@ static int set_fused_tiling(les_handle *h, int ty, int kc)
 }
 
 static int items_of(const FusedJet &F) { return F.nbx * F.nby * F.nkc; }
+static std::string kc_label(int kc)
+{
+    return kc == 0 ? std::string("balanced") : (kc < 0 ? std::string("lockstep") : std::to_string(kc));
+}
 static int autotune_fused(les_handle *h);
 
 // One fused stage (or residual) over all jets (jet < 0) or one jet.
@@ -450,14 +459,15 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     const FusedJet *fj = jet < 0 ? h->d_fj : h->d_fj1 + jet;
     const int nj = jet < 0 ? h->njets : 1;
     const int items = jet < 0 ? h->fused_items : items_of(h->fj[jet]);
+    const int tiles = jet < 0 ? h->fused_tiles : h->fj[jet].nbx * h->fj[jet].nby;
     const int grid = std::max(1, std::min(items, h->nsm * (h->fused_ty == 16 ? 1 : 2)));
     if (jet >= 0) jets += jet;
-    const int bal = h->fused_balanced ? 1 : 0;
+    const int bal = h->fused_balanced;
     if (h->fused_ty == 16)
-        launch_fused<16>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
+        launch_fused<16>(jets, fj, nj, items, tiles, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
                          h->stage_wait_limit, st);
     else
-        launch_fused<8>(jets, fj, nj, items, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
+        launch_fused<8>(jets, fj, nj, items, tiles, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
                          h->stage_wait_limit, st);
 }
 
@@ -1089,7 +1099,8 @@ static int autotune_fused(les_handle *h)
     }
     if (!cached) {
         const int tys[2] = {16, 8};
-        const int kcs[7] = {8, 16, 24, 48, 96, 100000, 0}; // 0: balanced tile-plane ranges
+        // 0: balanced tile-plane ranges; -1: whole-column waves, then balanced ranges
+        const int kcs[8] = {8, 16, 24, 48, 96, 100000, 0, -1};
         float best = 1e30f;
         EventPair ev;
         CK(cudaEventCreate(&ev.e0));
@@ -1115,9 +1126,8 @@ static int autotune_fused(les_handle *h)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         pick = g_tune_cache.emplace(key, pick).first->second;
     }
-    h->tune_note = "ty=" + std::to_string(pick.first) + " kc=" +
-                   (pick.second == 0 ? std::string("balanced") : std::to_string(pick.second)) +
-                   " (tuned over ty {16,8} x kc {8,16,24,48,96,all,balanced})";
+    h->tune_note = "ty=" + std::to_string(pick.first) + " kc=" + kc_label(pick.second) +
+                   " (tuned over ty {16,8} x kc {8,16,24,48,96,all,balanced,lockstep})";
     return set_fused_tiling(h, pick.first, pick.second);
 }
 
@@ -1227,11 +1237,11 @@ extern "C" int les_set_fused_tiling(les_handle *h, int ty, int kc)
 {
     if (!h) return LES_ERR_ARG;
     if (h->prec != LES_FP32) return fail(h, LES_ERR_ARG, "the fused tiling applies to FP32 handles");
-    if ((ty != 8 && ty != 16) || kc < 0) return fail(h, LES_ERR_ARG, "ty must be 8 or 16 and kc >= 0");
+    if ((ty != 8 && ty != 16) || kc < -1) return fail(h, LES_ERR_ARG, "ty must be 8 or 16 and kc >= -1");
     int rc = set_fused_tiling(h, ty, kc);
     if (rc) return rc;
     h->tuned = true;
-    h->tune_note = "ty=" + std::to_string(ty) + " kc=" + (kc == 0 ? std::string("balanced") : std::to_string(kc)) +
+    h->tune_note = "ty=" + std::to_string(ty) + " kc=" + kc_label(kc) +
                    " (set by the caller)";
     if (h->gexec) { // the captured step holds the old work list
         cudaGraphExecDestroy(h->gexec);

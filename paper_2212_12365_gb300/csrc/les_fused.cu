@@ -473,8 +473,8 @@ __device__ __forceinline__ D3 deriv_end(int t, const float4 &a1, const float2 &b
 template <int TY, bool SEP>
 __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
-            int total_items, int src, int dst, int stage, const double *__restrict__ dt, int rhs_only,
-            int balanced, int wait_limit)
+            int total_items, int total_tiles, int src, int dst, int stage, const double *__restrict__ dt,
+            int rhs_only, int balanced, int wait_limit)
 {
     using G_ = Geo<TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -486,11 +486,16 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     const int c2 = (ty + 1) * C2X + (tx + 1);
     const int c1 = tid;
 
-    // Work cursor: items (jet, tile, k-chunk) strided over the grid, or, in the
-    // balanced form, the CTA's contiguous share of all tile-planes (jet-major,
-    // tile, then plane), cut into one column piece per tile it touches; a
-    // piece starting mid-column recomputes its first zeta flux, so the result
-    // does not depend on where the cuts fall.
+    // Work cursor: items (jet, tile, k-chunk) strided over the grid
+    // (balanced = 0), or the CTA's contiguous, equal share of all tile-planes
+    // (jet-major, tile, then plane), cut into one column piece per tile it
+    // touches (balanced = 1).  balanced = 2 (lockstep) first runs
+    // total_tiles / gridDim.x waves of whole columns (tile blockIdx.x +
+    // wave * gridDim.x: the CTAs march k together, so neighbouring tiles read
+    // their shared halo planes within a short window, mostly from L2) and
+    // shares out the remaining tile-planes the same way.  A piece starting
+    // mid-column recomputes its first zeta flux, so the result does not
+    // depend on where the cuts fall.
     // general form: the TMA staging buffer must be 128-byte aligned (the
     // dynamic shared memory starts the window, so it is; checked anyway)
     const bool tma_smem_ok = (smem_u32(S.QG) & 127u) == 0;
@@ -504,11 +509,43 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
     if (tid == 0) mbar_init(S.MBAR);
     __syncthreads();
     int item = blockIdx.x, w = 0, wend = 0;
-    if (balanced) {
-        w = (int)(((long long)total_items * blockIdx.x) / gridDim.x);
-        wend = (int)(((long long)total_items * (blockIdx.x + 1)) / gridDim.x);
-    }
-    while (balanced ? w < wend : item < total_items) {
+    // balanced form: tile-plane ranges [w, wend), one per whole-column wave,
+    // then the share of the rest
+    const int nwave = balanced == 2 ? total_tiles / (int)gridDim.x : 0;
+    int wave = 0;
+    auto jet_of_tile = [&](int t) {
+        int lo = 0, hi = njets;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (fj[mid].tile0 <= t) lo = mid; else hi = mid;
+        }
+        return lo;
+    };
+    auto next_range = [&]() {
+        while (wave <= nwave) {
+            if (wave < nwave) {
+                const int t = blockIdx.x + wave * gridDim.x;
+                const FusedJet &Fw = fj[jet_of_tile(t)];
+                w = Fw.item0 + (t - Fw.tile0) * Fw.nkc;
+                wend = w + Fw.nkc;
+            } else {
+                const int t1 = nwave * gridDim.x;
+                int i1 = total_items;
+                if (t1 < total_tiles) {
+                    const FusedJet &Fw = fj[jet_of_tile(t1)];
+                    i1 = Fw.item0 + (t1 - Fw.tile0) * Fw.nkc;
+                }
+                const long long rem = total_items - i1;
+                w = i1 + (int)((rem * blockIdx.x) / gridDim.x);
+                wend = i1 + (int)((rem * (blockIdx.x + 1)) / gridDim.x);
+            }
+            ++wave;
+            if (w < wend) return true;
+        }
+        return false;
+    };
+    if (balanced) next_range();
+    while (balanced ? (w < wend || next_range()) : item < total_items) {
         const int key = balanced ? w : item;
         int jet = 0;
         {
@@ -988,25 +1025,25 @@ template <int TY> int fused_prepare()
 }
 
 template <int TY>
-void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid, int src,
-                  int dst, int stage, const double *dt, int rhs_only, int separable, int balanced, int wait_limit,
-                  cudaStream_t st)
+void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int total_tiles,
+                  int grid, int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
+                  int wait_limit, cudaStream_t st)
 {
     dim3 block(FX, TY);
     if (wait_limit < 0) wait_limit = MBAR_WAIT_LIMIT;
     if (separable)
-        k_fused<TY, true><<<grid, block, Geo<TY>::BYTES_SEP, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                              rhs_only, balanced, wait_limit);
+        k_fused<TY, true><<<grid, block, Geo<TY>::BYTES_SEP, st>>>(jets, fj, njets, total_items, total_tiles, src,
+                                                              dst, stage, dt, rhs_only, balanced, wait_limit);
     else
-        k_fused<TY, false><<<grid, block, Geo<TY>::BYTES_GEN, st>>>(jets, fj, njets, total_items, src, dst, stage, dt,
-                                                               rhs_only, balanced, wait_limit);
+        k_fused<TY, false><<<grid, block, Geo<TY>::BYTES_GEN, st>>>(jets, fj, njets, total_items, total_tiles, src,
+                                                               dst, stage, dt, rhs_only, balanced, wait_limit);
 }
 
 template int fused_prepare<16>();
 template int fused_prepare<8>();
-template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
+template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int, int,
                                const double *, int, int, int, int, cudaStream_t);
-template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int,
+template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int, int,
                               const double *, int, int, int, int, cudaStream_t);
 
 } // namespace les

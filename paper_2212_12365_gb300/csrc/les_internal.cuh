@@ -244,7 +244,8 @@ struct FusedParams {
 // the balanced form (kc == 0) the items are its tile-planes, nkc = the number
 // of planes per column, and every CTA takes one contiguous range of them.
 struct FusedJet {
-    int item0;
+    int item0;             // first work item of the jet
+    int tile0;             // first tile of the jet (balanced form)
     int nbx, nby, nkc;
     int kc;                 // planes per k-chunk (0: balanced form)
     FusedParams fp;
@@ -267,8 +268,8 @@ constexpr int TMA_BOX_X = 40;
 
 template <int TY> int fused_prepare();
 template <int TY>
-void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int grid,
-                  int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
+void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int total_tiles,
+                  int grid, int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
                   int wait_limit, cudaStream_t st);
 
 // Separable form: 1-D spacings of a Cartesian-product grid from device

@@ -274,7 +274,7 @@ def les_describe(h) -> str:
 
 
 def les_set_fused_tiling(h, ty: int, kc: int):
-    """Fix the fused FP32 stage's tile height (8 or 16) and k-chunk (0 = balanced)."""
+    """Fix the fused FP32 stage's tile height (8 or 16) and k-chunk (0 = balanced, -1 = lockstep)."""
     _check(h, lib().les_set_fused_tiling(h, int(ty), int(kc)))
 
 

@@ -38,6 +38,8 @@ GRIDS = {
     "mixed_periodic_z": lambda: (_mixed_periodic(), I.FlowParams(Re=2e3)),
     "tiny_4x4x4": lambda: (I.wavy_box_grid((4, 4, 4), amp=0.02), I.FlowParams(Re=100.0)),
     "polar": lambda: (I.polar_jet_grid(20, 10, 16, 6.0, 3.0), I.FlowParams(Re=1e4)),
+    # more tiles than CTAs: the lockstep form runs whole-column waves first
+    "wide": lambda: (I.jet_grid(400, 160, 12, 20.0, 10.0, 10.0, 0.125, 0.1), I.FlowParams(Re=1e4)),
 }
 
 # (grid, precision, tiling or None)
@@ -49,6 +51,7 @@ CASES = [
     ("mixed_periodic_z", les.LES_FP32, (8, 0)), ("mixed_periodic_z", les.LES_FP64, None),
     ("tiny_4x4x4", les.LES_FP64, None), ("tiny_4x4x4", les.LES_FP32, (8, 1)),
     ("polar", les.LES_FP64, None), ("polar", les.LES_FP32, (8, 100000)),
+    ("wide", les.LES_FP32, (8, -1)), ("wide", les.LES_FP32_SEPARABLE, (16, -1)),
 ]
 
 

@@ -129,13 +129,13 @@ def test_batched_fp32_against_oracle():
 def test_fused_stage_independent_of_tiling(prec):
     """Every work decomposition of the fused stage (tile height 8 or 16; fixed
     k-chunks, including a chunk of one plane; the balanced tile-plane ranges
-    whose cuts fall mid-column) gives the same bits, on a batch of uneven
-    jets."""
+    whose cuts fall mid-column; the lockstep form's whole-column waves before
+    them) gives the same bits, on a batch of uneven jets."""
     jets = I.batch_jets(4, seed=11)
     specs = [g for g, _ in jets]
     fps = [f for _, f in jets]
     out = []
-    for ty, kc in ((8, 100000), (16, 100000), (8, 1), (16, 5), (8, 0), (16, 0)):
+    for ty, kc in ((8, 100000), (16, 100000), (8, 1), (16, 5), (8, 0), (16, 0), (8, -1), (16, -1)):
         b = les.Solver(specs, fps, prec)
         for j, (g, f) in enumerate(jets):
             b.set_state(I.smooth_random_primitives(g, 40 + j, amp=0.05), jet=j)
@@ -152,7 +152,7 @@ def test_fused_stage_independent_of_tiling(prec):
 def test_fused_tiling_arguments_checked():
     spec, fp = I.jet_small()
     s = les.Solver(spec, fp, les.LES_FP32)
-    for ty, kc in ((4, 0), (8, -1)):
+    for ty, kc in ((4, 0), (8, -2)):
         with pytest.raises(les.LesError):
             les.les_set_fused_tiling(s.h, ty, kc)
     s.close()
@@ -250,3 +250,26 @@ def test_handles_stepped_from_two_host_threads():
         ref = [None, None]
         run(shapes[i], ref, i)
         np.testing.assert_array_equal(res[i], ref[i])
+
+
+@pytest.mark.parametrize("prec", [les.LES_FP32, les.LES_FP32_SEPARABLE])
+def test_lockstep_waves_bit_identical(prec):
+    """A grid with more tiles than CTAs (400 x 160 x 12: 378 tiles of 32 x 8,
+    168 of 32 x 16), so that the lockstep form runs a wave of whole columns
+    before sharing out the rest: the same bits as whole columns, k-chunks and
+    the balanced ranges."""
+    spec = I.jet_grid(400, 160, 12, 20.0, 10.0, 10.0, 0.125, 0.1)
+    fp = I.FlowParams(Re=1e4)
+    prim = I.smooth_random_primitives(spec, 5, amp=0.05)
+    out = []
+    for ty, kc in ((8, 100000), (8, 0), (8, -1), (16, -1), (16, 3)):
+        s = les.Solver(spec, fp, prec)
+        s.set_state(prim)
+        les.les_set_fused_tiling(s.h, ty, kc)
+        s.step(2)
+        out.append(s.get_state(les.LES_STATE_RAW))
+        if kc == -1:
+            assert "kc=lockstep" in les.les_describe(s.h)
+        s.close()
+    for o in out[1:]:
+        np.testing.assert_array_equal(o, out[0])
