@@ -524,7 +524,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 line of the FP64 default run")
     ap.add_argument("--probe", action="store_true", help="register the cylinder surface probe")
     ap.add_argument("--tiling", default=None,
-                    help="TY,KC: fix the fused FP32 stage's tile height and k-chunk (0 = balanced) "
+                    help="TY,KC: fix the fused FP32 stage's tile height and k-chunk (0 = balanced, -1 = lockstep) "
                          "instead of autotuning")
     ap.add_argument("--sweep", action="store_true",
                     help="throughput over the paper's ten mesh sizes (polar meshes), FP64 and FP32")
