@@ -53,6 +53,19 @@ TRAFFIC_BYTES_PER_POINT = {(_PAPER_JET, "fp64", "k_iface", None): 938.0,
                            (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=lockstep"): 63.9,
                            (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=balanced"): 93.9,
                            (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): 54.0}
+
+
+def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str):
+    """The captured DRAM bytes per point of the dominant kernel for this run's
+    workload, precision and (fused stage) decomposition, read from the
+    handle's description ("... ty=8 kc=lockstep ..."); None if not captured."""
+    decomp = None
+    if prec != "fp64":
+        mt = re.search(r"ty=(\d+) kc=(\w+)", describe)
+        decomp = f"ty={mt.group(1)} kc={mt.group(2)}" if mt else None
+    return TRAFFIC_BYTES_PER_POINT.get((workload, prec, kname, decomp))
+
+
 # Arithmetic-pipe utilisation of the dominant kernel from the same committed
 # ncu captures (sm__inst_executed_pipe_*, % of peak sustained while active)
 PIPE_UTIL_NCU = {("fp64", "k_iface"): {"sm__inst_executed_pipe_fp64": 0.872},
@@ -390,11 +403,7 @@ def run_ours(args):
     achieved = flops_pt * N / t_launch / 1e12
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6750.0)
-    decomp = None
-    if prec != "fp64":
-        mt = re.search(r"ty=(\d+) kc=(\w+)", les.les_describe(solver.h))
-        decomp = f"ty={mt.group(1)} kc={mt.group(2)}" if mt else None
-    traffic_pt = TRAFFIC_BYTES_PER_POINT.get((args.workload, prec, kname, decomp))
+    traffic_pt = traffic_bytes_per_point(args.workload, prec, kname, les.les_describe(solver.h))
     bytes_pt_stage = ALGO_BYTES_PER_PT_STAGE[prec]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_pt * N if traffic_pt else None,
