@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 from paper_2212_12365_gb300 import inputs as I  # noqa: E402
 
 # Algorithmic FP64/FP32 operations per grid point and stage, counted from the
-# method (each interface flux once; FMA = 2, divide/sqrt = 1): see the design
-# notes, section "Roofline".
+# method (each interface flux once; FMA = 2, divide/sqrt = 1): primitives 96,
+# gradients and closures 141, three interface fluxes 765, update 41.
 FLOPS_PER_PT_STAGE = {"point": 96, "grads": 141, "iface": 765, "update": 41}
 # Algorithmic HBM bytes per point and stage: stages 2-5 read Q(l-1), Q(0) and 10
 # metric values and write Q(l); stage 1 reads Q(0) once: 24 values on average.
@@ -42,38 +42,51 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
 # DRAM bytes per point of one launch of the dominant kernel in the launch
 # configuration of the run, from the ncu captures summarised in profiles/:
 # keyed by workload, precision, kernel and (fused stage) the decomposition in
-# use (the tuner's pick on the paper-scale jet is one of those listed).  None
-# for anything not captured, and once the kernel has changed since the
-# capture.
+# use.  Each capture records the SHA-256 prefix of the kernel's source file
+# at capture time; when the file has changed since, the figure no longer
+# describes the kernel that runs and the lookup gives None.
 _PAPER_JET = "jet-384x256x144"
-TRAFFIC_BYTES_PER_POINT = {(_PAPER_JET, "fp64", "k_iface", None): 938.0,
-                           (_PAPER_JET, "fp32", "k_fused", "ty=8 kc=lockstep"): 148.3,
-                           (_PAPER_JET, "fp32", "k_fused", "ty=8 kc=balanced"): 196.7,
-                           (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): 128.1,
-                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=lockstep"): 63.9,
-                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=8 kc=balanced"): 93.9,
-                           (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): 54.0}
+KERNEL_SOURCE = {"k_iface": "les_stage.cu", "k_fused": "les_fused.cu"}
+TRAFFIC_BYTES_PER_POINT = {}  # (workload, precision, kernel, decomposition) -> (bytes per point, source sha16)
 
 
-def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str):
+def source_sha16(kname: str):
+    """SHA-256 prefix of the source file that holds kernel kname."""
+    import hashlib
+    f = KERNEL_SOURCE.get(kname)
+    if not f:
+        return None
+    path = os.path.join(ROOT, "paper_2212_12365_gb300", "csrc", f)
+    try:
+        return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str, table=None):
     """The captured DRAM bytes per point of the dominant kernel for this run's
     workload, precision and (fused stage) decomposition, read from the
-    handle's description ("... ty=8 kc=lockstep ..."); None if not captured."""
+    handle's description ("... ty=8 kc=lockstep ..."); None if not captured
+    or if the kernel's source changed after the capture."""
+    table = TRAFFIC_BYTES_PER_POINT if table is None else table
     decomp = None
     if prec != "fp64":
         mt = re.search(r"ty=(\d+) kc=(\w+)", describe)
         decomp = f"ty={mt.group(1)} kc={mt.group(2)}" if mt else None
-    return TRAFFIC_BYTES_PER_POINT.get((workload, prec, kname, decomp))
+    hit = table.get((workload, prec, kname, decomp))
+    if hit is None or hit[1] != source_sha16(kname):
+        return None
+    return hit[0]
 
 
-# Arithmetic-pipe utilisation of the dominant kernel from the same committed
-# ncu captures (sm__inst_executed_pipe_*, % of peak sustained while active)
-PIPE_UTIL_NCU = {("fp64", "k_iface"): {"sm__inst_executed_pipe_fp64": 0.872},
-                 ("fp32", "k_fused"): {"sm__inst_executed_pipe_fma": 0.292, "sm__inst_executed_pipe_alu": 0.253,
-                                       "smsp__issue_active": 0.528}}
-# Nominal FP64 FMA throughput of GB300: 2 DFMA / clock / SM x 152 SMs x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Arithmetic-pipe utilisation of the dominant kernel from the committed ncu
+# captures (sm__inst_executed_pipe_*, % of peak sustained while active), with
+# the source hash of the captured kernel as above
+PIPE_UTIL_NCU = {}  # (precision, kernel) -> (metrics dict, source sha16)
+# Nominal multiply-add throughput of GB300 (unit counts x the maximum clock),
+# reported beside the measured figures: 2 DFMA and 128 FFMA per clock and SM.
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
 def _batch64():
@@ -285,6 +298,104 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def hbm_peak_gbs():
+    """HBM denominator: the measured copy bandwidth of this machine's
+    GB300s, or the profiling recipe's fallback figure when that file is
+    missing (labelled as such)."""
+    v = measured_peaks().get("hbm_gbs")
+    if v:
+        return float(v), "measured (MEASURED_PEAKS.json, copy bandwidth)"
+    return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json missing)"
+
+
+_ALU = {}
+
+
+def alu_peaks(les):
+    """Measured multiply-add throughput of this GPU (TFLOP/s): FP64 DFMA, FP32
+    FFMA and paired FP32 (fma.rn.f32x2), each a short independent-chain loop
+    timed with CUDA events (les_measure_peak); measured once per process."""
+    if not _ALU:
+        _ALU["fp64_fma"] = les.les_measure_peak(les.LES_PEAK_FP64_FMA)
+        _ALU["fp32_fma"] = les.les_measure_peak(les.LES_PEAK_FP32_FMA)
+        _ALU["fp32x2_fma"] = les.les_measure_peak(les.LES_PEAK_FP32X2_FMA)
+    return dict(_ALU)
+
+
+def _time_steps(solver, steps, torch):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    solver.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def batched_form(args, les, torch, fp64_value):
+    """The batched form (64 jets of uneven grids, Mach, temperature ratio,
+    Reynolds number and seed, one persistent launch per stage, the step a
+    CUDA graph), FP32 and FP32 with separable metrics: device rate after the
+    warm-up, the HBM fraction of the algorithmic bytes, and a bit-for-bit
+    check of three jets against single-jet handles after the same steps."""
+    specs, fps = _batch64()
+    N = sum(g.N for g in specs)
+    hbm, _ = hbm_peak_gbs()
+    out = {"jets": len(specs), "points": N}
+    check_jets = (0, len(specs) // 2, len(specs) - 1)
+    nchk = 3
+    for name, P in (("fp32", les.LES_FP32), ("fp32-sep", les.LES_FP32_SEPARABLE)):
+        b = les.Solver(specs, fps, P)
+        for j, (g, f) in enumerate(zip(specs, fps)):
+            b.set_state(I.ambient_primitives(g.N, f.TR), les.LES_STATE_PRIMITIVE, jet=j)
+        b.step(nchk)
+        same = True
+        for j in check_jets:
+            s1 = les.Solver(specs[j], fps[j], P)
+            s1.set_state(I.ambient_primitives(specs[j].N, fps[j].TR), les.LES_STATE_PRIMITIVE)
+            s1.step(nchk)
+            same = same and bool(np.array_equal(s1.get_state(les.LES_STATE_RAW),
+                                                b.get_state(les.LES_STATE_RAW, jet=j)))
+            s1.close()
+        b.step(args.warmup)
+        ms = _time_steps(b, args.steps, torch)
+        v = N * 5 * args.steps / (ms / 1e3)
+        out[name] = {"value": v, "ms_per_step": ms / args.steps, "speedup_vs_fp64_single_jet": v / fp64_value,
+                     "hbm_frac_algorithmic": v * ALGO_BYTES_PER_PT_STAGE[name] / 1e9 / hbm,
+                     "bit_identical_to_single_jets": {"jets": list(check_jets), "after_steps": nchk,
+                                                      "equal": same},
+                     "stage": les.les_describe(b.h)}
+        b.close()
+    return out
+
+
+def large_probe_form(args, les, torch):
+    """The large FP32 run: 768x384x192 (56.6 M points), Mach 1.4, temperature
+    ratio 2, with the cylinder surface probe (r = 3D, 256 x 384 points, every
+    5 steps) written to a device ring inside the captured step."""
+    spec, fp = I.jet_large()
+    s = les.Solver(spec, fp, les.LES_FP32)
+    s.set_state(I.ambient_primitives(spec.N, fp.TR), les.LES_STATE_PRIMITIVE)
+    xyz = I.cylinder_points(3.0, 256, 384, 0.5, spec.x.max() - 0.5)
+    cap = 64
+    ring = torch.zeros((cap, 5, xyz.shape[1]), device="cuda", dtype=torch.float32)
+    les.les_probe_surface(s.h, xyz, 5, ring.data_ptr(), cap)
+    s.step(args.warmup)
+    ms = _time_steps(s, args.steps, torch)
+    v = spec.N * 5 * args.steps / (ms / 1e3)
+    frames = les.les_probe_frames(s.h)
+    hbm, _ = hbm_peak_gbs()
+    out = {"workload": "jet-768x384x192", "precision": "fp32", "points": spec.N, "value": v,
+           "ms_per_step": ms / args.steps,
+           "hbm_frac_algorithmic": v * ALGO_BYTES_PER_PT_STAGE["fp32"] / 1e9 / hbm,
+           "probe": {"points": int(xyz.shape[1]), "every": 5, "frames": int(frames),
+                     "finite": bool(torch.isfinite(ring).all().item())},
+           "stage": les.les_describe(s.h)}
+    s.close()
+    return out
+
+
 def precision_form(args, spec, fp, les, torch, fp64_value):
     """FP32 storage/arithmetic on the same grid (metrics and sums in FP64): its
     rate, speedup over the FP64 path, and relative L2 per field against the FP64
@@ -321,8 +432,7 @@ def precision_form(args, spec, fp, les, torch, fp64_value):
         f["speedup_vs_fp64"] = f["value"] / fp64_value
         f["rel_l2_vs_fp64_per_field"] = [float(e) for e in err]
         f["after_steps"] = steps
-        f["hbm_frac_algorithmic"] = f["value"] * ALGO_BYTES_PER_PT_STAGE[names[prec]] / 1e9 / \
-            measured_peaks().get("hbm_gbs", 6750.0)
+        f["hbm_frac_algorithmic"] = f["value"] * ALGO_BYTES_PER_PT_STAGE[names[prec]] / 1e9 / hbm_peak_gbs()[0]
     out = forms[les.LES_FP32]
     # the separable-metric stage (Cartesian-product grids only), reported apart
     out["separable"] = forms[les.LES_FP32_SEPARABLE]
@@ -393,31 +503,38 @@ def run_ours(args):
     # per-kernel device time of the same stage sequence, eager with events
     prof = les.les_profile_step(solver.h, max(1, min(args.steps, 3)))
     tot = sum(v[0] for v in prof.values())
+    alu = alu_peaks(les)
     if prec == "fp64":
         dom = max(FLOPS_PER_PT_STAGE, key=lambda k: prof[k][0])
-        kname, flops_pt, peak = f"k_{dom}", FLOPS_PER_PT_STAGE[dom], FP64_PEAK_TFLOPS
+        kname, flops_pt = f"k_{dom}", FLOPS_PER_PT_STAGE[dom]
+        peak, peak_nominal = alu["fp64_fma"], FP64_NOMINAL_TFLOPS
+        peak_source = "measured: DFMA loop of les_measure_peak on this GPU (CUDA events)"
     else:
         dom = "iface"  # the fused single-pass stage kernel is traced under this kind
-        kname, flops_pt, peak = "k_fused", sum(FLOPS_PER_PT_STAGE.values()), FP32_PEAK_TFLOPS
+        kname, flops_pt = "k_fused", sum(FLOPS_PER_PT_STAGE.values())
+        peak, peak_nominal = alu["fp32_fma"], FP32_NOMINAL_TFLOPS
+        peak_source = "measured: FFMA loop of les_measure_peak on this GPU (CUDA events)"
     t_launch = prof[dom][0] / max(prof[dom][1], 1) / 1e3  # s per launch
     achieved = flops_pt * N / t_launch / 1e12
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs", 6750.0)
+    hbm_peak, hbm_source = hbm_peak_gbs()
     traffic_pt = traffic_bytes_per_point(args.workload, prec, kname, les.les_describe(solver.h))
+    pipe = PIPE_UTIL_NCU.get((prec, kname))
     bytes_pt_stage = ALGO_BYTES_PER_PT_STAGE[prec]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_pt * N if traffic_pt else None,
-                "pipe_util_ncu": PIPE_UTIL_NCU.get((prec, kname)),
-                "peak_source": f"nominal {'FP64' if prec == 'fp64' else 'FP32'} unit count x 2.07 GHz "
-                               "(not in MEASURED_PEAKS.json)",
+                "pipe_util_ncu": pipe[0] if pipe and pipe[1] == source_sha16(kname) else None,
+                "peak_source": peak_source,
+                "peak_nominal": peak_nominal, "frac_nominal": achieved / peak_nominal,
+                "measured_alu_peaks_tflops": alu,
                 "flops_per_point_stage": flops_pt,
                 "share": prof[dom][0] / tot if tot else None,
                 "per_kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
                 "stage": les.les_describe(solver.h),
+                "source_sha16": source_sha16(kname),
                 # the metric's "% HBM roofline": algorithmic bytes of a stage at the achieved rate
                 "hbm_view": {"algorithmic_bytes_per_point_stage": bytes_pt_stage,
                              "achieved_gbs": value * bytes_pt_stage / 1e9 / ws,
-                             "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)",
+                             "peak_gbs": hbm_peak, "peak_source": hbm_source,
                              "frac": value * bytes_pt_stage / 1e9 / ws / hbm_peak,
                              "frac_nominal": value * bytes_pt_stage / 1e9 / ws / HBM_NOMINAL_GBS,
                              # DRAM bytes of the dominant kernel (ncu capture) over its event-timed launch
@@ -454,9 +571,15 @@ def run_ours(args):
         if one:
             cpu["value_1core"] = one["value"]
             cpu["sample_1core"] = one["sample"] + ", 1 thread"
-    secondary = None
-    if rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64" and not args.no_fp32:
+    secondary = batched = large = None
+    default_run = rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64"
+    if default_run and not args.no_fp32:
         secondary = precision_form(args, spec, fp, les, torch, value)
+    if default_run and not args.no_extra:
+        solver.close()
+        solver = None
+        batched = batched_form(args, les, torch, value)
+        large = large_probe_form(args, les, torch)
 
     if rank == 0:
         line = {"metric": "grid-point-stage updates/s", "value": value,
@@ -472,9 +595,12 @@ def run_ours(args):
                                            "frames": les.les_probe_frames(solver.h)}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "precision_form": secondary,
+                "batched": batched,
+                "large_probe": large,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    solver.close()
+    if solver is not None:
+        solver.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -531,6 +657,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 line of the FP64 default run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (64 jets) and large probed (768x384x192) keys of the default run")
     ap.add_argument("--probe", action="store_true", help="register the cylinder surface probe")
     ap.add_argument("--tiling", default=None,
                     help="TY,KC: fix the fused FP32 stage's tile height and k-chunk (0 = balanced, -1 = lockstep) "

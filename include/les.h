@@ -181,7 +181,10 @@ int les_step(les_handle *h, int nsteps);
  * the handle was created.  The stage then reads that plane, and every later
  * one of the launch, directly from global memory, so q is still written and
  * holds the state a normal step gives; the handle keeps reporting the
- * timeout (it points to a stalled copy engine). */
+ * timeout (it points to a stalled copy engine).  If the stage's final,
+ * bounded wait for such an abandoned copy gives up as well, the copy may
+ * still land in shared memory another CTA uses: the call then returns
+ * LES_ERR_CUDA, q is still written but the state is unreliable. */
 int les_get_state(les_handle *h, double *q, int kind);
 int les_get_state_jet(les_handle *h, int jet, double *q, int kind);
 
@@ -271,8 +274,9 @@ int64_t les_last_launch_count(les_handle *h);
  * site 1 a point index (value = k << 32 | j << 16 | i, 16 bits each), 2-4 a
  * fused-stage global offset (state, static record, update), 5-7 a fused-stage
  * shared-memory slot (point ring, plane tables, eta-flux rows).  In every
- * build, site 8 records a staging wait of the fused stage that gave up (see
- * les_get_state); in a normal build no other site is recorded.
+ * build, site 8 records a staging wait of the fused stage that gave up and
+ * site 9 an abandoned staging copy that did not complete before its CTA
+ * exited (see les_get_state); in a normal build no other site is recorded.
  * Synchronises the stream.  Errors: LES_ERR_ARG. */
 int les_bounds_checking(void);
 int les_bounds_violation(les_handle *h, uint64_t *out);
@@ -303,6 +307,21 @@ int les_bounds_violation(les_handle *h, uint64_t *out);
 #define LES_NOALLOC_MAX_POINTS 268435456LL
 int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints, double *out,
                           void *stream);
+
+/* Measured arithmetic throughput of the current device, for the compute-bound
+ * roofline fractions reported beside the stage timings (the paper has no
+ * counterpart: it is a measurement utility).  kind 0: FP64 fused multiply-add
+ * (DFMA); 1: FP32 fused multiply-add (FFMA); 2: paired FP32 fused multiply-add
+ * (fma.rn.f32x2, two lanes per instruction).  Launches a short loop of
+ * independent multiply-add chains on the legacy default stream (timed with
+ * CUDA events, best of three after a warm-up; a few milliseconds) and writes
+ * the achieved rate in TFLOP/s (FMA = 2 FLOP) to *tflops.  Synchronises the
+ * device's default stream.  Errors: LES_ERR_ARG (null pointer, unknown kind),
+ * LES_ERR_CUDA. */
+#define LES_PEAK_FP64_FMA 0
+#define LES_PEAK_FP32_FMA 1
+#define LES_PEAK_FP32X2_FMA 2
+int les_measure_peak(int kind, double *tflops);
 
 /* Human-readable description of a handle: precision, jets, device bytes and
  * the stage kernel configuration chosen by the autotuner (FP32: fused tile

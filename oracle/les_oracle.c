@@ -24,8 +24,8 @@
  *                                             jet entrance, exit, periodic,
  *                                             boundary 4th-difference fix
  *
- * Readings adopted where the paper is garbled or silent (each is listed in
- * the design notes with its justification):
+ * Readings adopted where the paper is garbled or silent, each with the
+ * reason it is taken:
  *   R1  heat flux q_j = -(k + k_sgs) dT/dx_j (sign of Eq. for q).
  *   R2  deviatoric strain S_ij - delta_ij S_kk / 3 (delta_ij missing).
  *   R3  eta-row metric terms are the standard cofactors; all nine are
@@ -48,13 +48,18 @@
  *   R13 RK on Qhat = J^-1 Q with RHS = sum of interface-flux differences.
  *   R14 R+ = q_ne + 2 c_e/(gamma-1); velocity corrected along the unit
  *       outward normal of the face.  The paper's subsonic exit and entrance
- *       ranges 0 < q_ne/a_e < 1 and -1 < q_ne/a_e < 0 leave q_ne = 0 open;
- *       a normal Mach number within 1e-8 of zero counts as zero and takes
- *       the exit side, so that a fluid at rest, or the first weak waves
- *       reaching a boundary from it (where q_ne crosses zero at rounding
- *       level), picks the same branch in every evaluation order; the two
- *       branches differ there by the tangential velocity and entropy of
- *       such waves only.
+ *       ranges 0 < q_ne/a_e < 1 and -1 < q_ne/a_e < 0 leave q_ne = 0 open,
+ *       and the face state jumps there (tangential velocity and entropy come
+ *       from inside on one side, from the freestream on the other), so a
+ *       sign decided by rounding is not reproducible.  A normal Mach number
+ *       within 1e-8 of zero counts as zero and takes the exit side.  Width:
+ *       two FP64 evaluations of the same flow (another operation order,
+ *       another machine) agree to about 1e-13 after the 10 steps the
+ *       parity bar covers, so a fluid at rest, where q_ne is zero up to that
+ *       rounding, decides alike on both; 1e-8 is five decades above that
+ *       level and three below the normal Mach number of the weakest
+ *       physical wave the configurations send to a boundary (the inflow
+ *       noise, 1e-3 of the jet velocity, arrives there at 1e-5 or more).
  *   R15 inflow: tanh profile of momentum thickness theta, Crocco-Busemann
  *       temperature, uniform pressure, per-step SplitMix64 velocity noise,
  *       Dirichlet where the profile is >= 0.01, far field elsewhere.

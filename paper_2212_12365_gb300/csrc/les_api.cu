@@ -128,6 +128,10 @@ static int wait_status(les_handle *h)
     unsigned long long v = 0;
     CK(cudaMemcpyAsync(&v, h->d_oob, sizeof(v), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if ((v >> 48) == 9)
+        return fail(h, LES_ERR_CUDA,
+                    "a staging copy of the fused stage did not complete even after the stage stopped "
+                    "waiting for it: the state is unreliable");
     if ((v >> 48) == 8)
         return fail(h, LES_ERR_TIMEOUT,
                     "a staging wait of the fused stage gave up (the stage fell back to direct loads)");

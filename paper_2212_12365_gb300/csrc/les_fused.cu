@@ -1006,8 +1006,14 @@ __global__ void __launch_bounds__(FX * TY, TY <= 8 ? 2 : 1)
         }
     }
     // a copy whose wait gave up may still be in flight into this CTA's
-    // shared memory: its issuer waits for it (bounded) before exiting
-    if (pend && tid == 0) mbar_wait(S.MBAR, tpar, MBAR_WAIT_LIMIT);
+    // shared memory: its issuer waits for it (bounded) before exiting; if
+    // that wait gives up too, the copy may land in the shared memory of the
+    // next CTA on this SM, which is recorded as site 9 (it outranks site 8:
+    // the state can no longer be trusted)
+    if (pend && tid == 0 && !mbar_wait(S.MBAR, tpar, MBAR_WAIT_LIMIT)) {
+        const JetDev<float> &J0 = jets[0];
+        if (J0.oob) atomicMax(J0.oob, 9ull << 48);
+    }
 }
 
 #undef CK_G

@@ -617,9 +617,9 @@ __global__ void __launch_bounds__(BLOCK) k_dt_max(const JetDev<real> *__restrict
 
 // ---------------------------------------------------------------------------
 // Diagnostics: per-block partials in a fixed order, then one block combines.
-// partial layout (16 doubles): [0] max|RHS_rho|, [1..5] sum RHS^2,
-// [6..10] Neumaier sums of Qhat, [11..15] their compensations; nonfinite
-// count is folded into [0] as NaN.
+// partial layout (NPART = 17 doubles): [0] max|RHS_rho|, [1..5] sum RHS^2,
+// [6..10] Neumaier sums of Qhat, [11..15] their compensations, [16] the
+// count of non-finite state or residual values (reported as out[11]).
 // ---------------------------------------------------------------------------
 
 constexpr int NPART = 17;

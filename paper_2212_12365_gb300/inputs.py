@@ -99,7 +99,9 @@ def jet_grid(ni: int, nj: int, nk: int, Lx: float, Ly: float, Lz: float,
 
 
 # ---------------------------------------------------------------------------
-# Named workloads (the paper's jet run shapes; see the design notes)
+# Named workloads: synthetic stand-ins for the paper's jet run (Sec. "Numerical
+# Results": Mach 1.4, temperature ratio 1, about 14 M points on a tanh-refined
+# mesh), at the sizes of the measured configurations
 # ---------------------------------------------------------------------------
 
 def jet_small() -> tuple[GridSpec, FlowParams]:

@@ -35,7 +35,7 @@ EXPORTED = [
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
     "les_set_fused_tiling", "les_debug_stage_wait", "les_last_launch_count", "les_bounds_checking", "les_bounds_violation",
-    "les_diag_sums_noalloc", "les_describe",
+    "les_diag_sums_noalloc", "les_measure_peak", "les_describe",
     "les_last_error", "les_destroy",
 ]
 
@@ -103,6 +103,7 @@ def lib():
         L.les_bounds_checking.argtypes = []
         L.les_bounds_violation.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.les_measure_peak.argtypes = [ctypes.c_int, _dp]
         L.les_describe.argtypes = [vp]
         L.les_describe.restype = ctypes.c_char_p
         L.les_last_error.argtypes = [vp]
@@ -316,6 +317,17 @@ def les_diag_sums_noalloc(qhat_ptr: int, rhs_ptr: int, npoints: int, out_ptr: in
     return int(lib().les_diag_sums_noalloc(ctypes.c_void_p(qhat_ptr), ctypes.c_void_p(rhs_ptr),
                                            int(npoints), ctypes.c_void_p(out_ptr),
                                            stream if stream is not None else current_stream()))
+
+
+LES_PEAK_FP64_FMA, LES_PEAK_FP32_FMA, LES_PEAK_FP32X2_FMA = 0, 1, 2
+
+
+def les_measure_peak(kind: int) -> float:
+    """Measured multiply-add throughput of the current device in TFLOP/s
+    (kind: LES_PEAK_FP64_FMA, LES_PEAK_FP32_FMA or LES_PEAK_FP32X2_FMA)."""
+    v = ctypes.c_double(0.0)
+    _check(None, lib().les_measure_peak(int(kind), ctypes.byref(v)))
+    return float(v.value)
 
 
 def les_destroy(h):

@@ -64,3 +64,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                    buf.data_ptr())
     assert rc == les.LES_ERR_ARG
     assert les.les_diag_sums_noalloc(buf.data_ptr(), buf.data_ptr(), 0, buf.data_ptr()) == les.LES_ERR_ARG
+
+
+def test_noalloc_multi_block_sums_against_host():
+    """3 x 65,536 + 17 points: three full reduction blocks and a partial one,
+    so the cross-block combine (maximum, sums of squares, Neumaier merge of
+    the per-block sums with their compensations, non-finite count) runs.
+    Two calls in a row on different data, compared with sums formed on the
+    host (math.fsum, exactly rounded); the second input plants two non-finite
+    values in different blocks."""
+    import math
+    import torch
+    n = 3 * 65536 + 17
+    rng = np.random.default_rng(31)
+    out = torch.full((12,), float("nan"), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        q = rng.normal(1.0, 0.3, (5, n)) * (1.0 + 1e3 * (rng.uniform(size=(5, n)) < 1e-3))
+        r = rng.normal(0.0, 1e-2, (5, n))
+        r[:, -5:] = 0.0
+        nbad = 0
+        if call == 1:
+            q[2, 70000] = np.inf
+            r[4, 150000] = np.nan
+            nbad = 2
+        dq = torch.from_numpy(q).cuda()
+        dr = torch.from_numpy(r).cuda()
+        out.fill_(float("nan"))
+        rc = les.les_diag_sums_noalloc(dq.data_ptr(), dr.data_ptr(), n, out.data_ptr())
+        assert rc == les.LES_OK
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert o[11] == nbad
+        if nbad:
+            continue
+        assert o[0] == np.abs(r[0]).max()
+        np.testing.assert_allclose(o[1:6], np.sqrt((r ** 2).sum(axis=1)), rtol=1e-12)
+        for f in range(5):
+            exact = math.fsum(q[f])
+            assert abs(o[6 + f] - exact) <= 4 * np.finfo(float).eps * abs(exact), f
