@@ -237,7 +237,8 @@ int les_debug_field(les_handle *h, int jet, int field, double *out);
 int les_profile_step(les_handle *h, int nsteps, double *ms_out, int64_t *counts);
 
 /* Work decomposition of the fused FP32 stage (LES_FP32, LES_FP32_SEPARABLE
- * handles): ty = 8 or 16 grid rows per CTA tile (32 x ty threads), kc >= 1
+ * handles): ty = 8 or 16 grid rows per CTA tile (32 x ty/2 threads, two rows
+ * each), kc >= 1
  * planes per k-chunk item, kc = 0 for the balanced form (every CTA of the
  * persistent grid takes one contiguous, equal share of all tile-planes), or
  * kc = -1 for the lockstep form (whole columns in waves of one tile per CTA,

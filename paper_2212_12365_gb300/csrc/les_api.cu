@@ -34,7 +34,7 @@ struct JetHost {
     char *met, *q[3], *prim, *grad, *hflux, *rhs;
     double *jinv64, *inflow_r;
     float4 *h1[3];                     // FP32: 1-D spacings of a product grid (separable form)
-    float4 *mp;                        // FP32 general form: packed static fields (4 float4 / point)
+    float4 *mp;                        // FP32 general form: paired static records (8 float4 / row pair)
     int nblk_pt, nblk_bc[3];
 };
 
@@ -85,6 +85,7 @@ struct les_handle {
     int fused_ty = 16;
     int fused_balanced = 0; // 0: k-chunk items, 1: balanced ranges, 2: lockstep waves, then balanced ranges
     int fused_items = 0, fused_tiles = 0;
+    int fused_cps[2] = {1, 1}; // resident CTAs per SM of the fused stage at tile height 8, 16
     bool tuned = false;
     std::string tune_note;
     int64_t launches_per_step = 0;
@@ -226,7 +227,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     size_t o_inr = take((size_t)g->nj * g->nk * 8);
     size_t o_h1 = prec == LES_FP32 ? take((size_t)(g->ni + g->nj + g->nk) * 16) : 0;
     const bool packed = g->precision == LES_FP32; // general FP32 form only
-    size_t o_mp = packed ? take((size_t)J.npad * 64) : 0;
+    size_t o_mp = packed ? take((size_t)g->nk * ((g->nj + 1) / 2) * J.pitch * 128) : 0;
     J.bytes = off;
     // store offsets relative to the jet region in the pointers for now
     J.met = (char *)o_met;
@@ -364,7 +365,7 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
         CK(cudaMemcpyAsync(J.jinv64, met64 + MET_JINV * J.fs, (size_t)J.fs * 8,
                            cudaMemcpyDeviceToDevice, h->st));
         if (J.mp) {
-            launch_pack_metrics((const float *)J.met, J.fs, J.mp, J.npad, h->st);
+            launch_pack_pairs((const float *)J.met, J.fs, J.pitch, J.n[1], J.n[2], J.mp, h->st);
             CK(cudaGetLastError());
         }
     }
@@ -464,7 +465,7 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     const int nj = jet < 0 ? h->njets : 1;
     const int items = jet < 0 ? h->fused_items : items_of(h->fj[jet]);
     const int tiles = jet < 0 ? h->fused_tiles : h->fj[jet].nbx * h->fj[jet].nby;
-    const int grid = std::max(1, std::min(items, h->nsm * (h->fused_ty == 16 ? 1 : 2)));
+    const int grid = std::max(1, std::min(items, h->nsm * h->fused_cps[h->fused_ty == 16 ? 1 : 0]));
     if (jet >= 0) jets += jet;
     const int bal = h->fused_balanced;
     if (h->fused_ty == 16)
@@ -496,7 +497,7 @@ static EncodeTiledFn encode_tiled()
 }
 
 // TMA maps of one FP32 jet's three state registers for the fused stage's
-// staging box (5 fields x 1 plane x (TY + 2) rows x 40 columns) at TY = 8 and
+// staging box (5 fields x 1 plane x (TY + 4) rows x 40 columns) at TY = 8 and
 // 16: tensor [field][k][j][i] with the padded row and field strides, columns
 // beyond ni read as zero.  Returns false if the encoder refuses.
 static bool make_state_maps(const JetHost &J, CUtensorMap out[6])
@@ -507,7 +508,7 @@ static bool make_state_maps(const JetHost &J, CUtensorMap out[6])
     const cuuint64_t strides[3] = {(cuuint64_t)J.pitch * 4, (cuuint64_t)J.pitch * J.n[1] * 4, (cuuint64_t)J.fs * 4};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int t = 0; t < 2; ++t) {
-        const cuuint32_t box[4] = {(cuuint32_t)TMA_BOX_X, (cuuint32_t)(t == 0 ? 10 : 18), 1, 5};
+        const cuuint32_t box[4] = {(cuuint32_t)TMA_BOX_X, (cuuint32_t)tma_box_rows(t == 0 ? 8 : 16), 1, 5};
         for (int r = 0; r < 3; ++r)
             if (enc(&out[3 * t + r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J.q[r], dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -621,6 +622,8 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     if (h->prec == LES_FP32) {
         if (fused_prepare<16>() != 0 || fused_prepare<8>() != 0)
             return bail(fail(h, LES_ERR_CUDA, "fused kernel shared-memory attribute"));
+        h->fused_cps[0] = fused_ctas_per_sm(8, h->sep ? 1 : 0);
+        h->fused_cps[1] = fused_ctas_per_sm(16, h->sep ? 1 : 0);
         h->fj.resize(njets);
         for (int j = 0; j < njets; ++j) {
             FusedParams &F = h->fj[j].fp;
@@ -640,6 +643,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
             F.pinf = (float)(1.0 / pp.gamma);
             for (int a = 0; a < 3; ++a) h->fj[j].h1[a] = h->J[j].h1[a];
             h->fj[j].mp = h->J[j].mp;
+            h->fj[j].njp = (h->J[j].n[1] + 1) / 2;
             h->fj[j].tmap = nullptr;
         }
         // TMA maps for jets whose i and j axes are not periodic (a periodic

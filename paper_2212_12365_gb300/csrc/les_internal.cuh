@@ -248,33 +248,42 @@ struct FusedJet {
     int tile0;             // first tile of the jet (balanced form)
     int nbx, nby, nkc;
     int kc;                 // planes per k-chunk (0: balanced form)
+    int njp;                // row pairs per column of the paired static records, (nj + 1) / 2
     FusedParams fp;
     // separable form (Cartesian-product grid): per axis a, for each index,
     // (h, 1/h, h^(2/3), 0) with h the derivative of coordinate a along axis a
     const float4 *h1[3];
-    // general form: the static fields of each point packed as four float4
-    // records (m0..m3 | m4..m7 | m8, J^-1, (Cs Delta)^2, J | row norms, 0)
+    // general form: the static fields of the two points of each row pair
+    // (rows 2p, 2p+1) of a column, interleaved point by point in eight
+    // float4: (m0 m1) (m2 m3) (m4 m5) (m6 m7) (m8, J^-1) ((Cs Delta)^2 J, J)
+    // (n0 n1) (n2, 0), m = the metric cofactors, n = the row norms; record of
+    // (i, pair p, k) at ((k * njp + p) * pitch + i) * 8
     const float4 *mp;
-    // general form, jets with no periodic i or j axis: tensor maps of the
-    // three state registers for the TMA staging of the next plane (null:
-    // plain loads)
+    // jets with no periodic i or j axis: tensor maps of the three state
+    // registers for the TMA staging of the next plane (null: plain loads)
     const CUtensorMap *tmap;
 };
 
-// TMA staging box of the fused stage: 5 fields x 1 plane x (TY + 2) rows x
+// TMA staging box of the fused stage: 5 fields x 1 plane x (TY + 4) rows x
 // 40 columns (the tile's 34 columns plus up to 3 for aligning the start
 // column down to a multiple of 4, i.e. 16 bytes).
 constexpr int TMA_BOX_X = 40;
+constexpr int tma_box_rows(int ty) { return ty + 4; }
 
 template <int TY> int fused_prepare();
+// resident CTAs per SM of the fused stage for tile height ty (general or
+// separable form), from the occupancy calculator; 1 if it cannot tell
+int fused_ctas_per_sm(int ty, int separable);
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int total_tiles,
                   int grid, int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
                   int wait_limit, cudaStream_t st);
 
+// General FP32 form: the paired static records (see FusedJet::mp) from the
+// FP32 static fields; mp holds nk * ((nj + 1) / 2) * pitch * 8 float4.
+void launch_pack_pairs(const float *met, long long fs, int pitch, int nj, int nk, float4 *mp, cudaStream_t st);
 // Separable form: 1-D spacings of a Cartesian-product grid from device
 // coordinates (FP64 derivative stencils of the metric computation).
-void launch_pack_metrics(const float *met, long long fs, float4 *mp, long long npad, cudaStream_t st);
 void launch_sep_metrics(const double *x, const double *y, const double *z, const int n[3], const int per[3],
                         const double shift[9], float4 *h1x, float4 *h1y, float4 *h1z, cudaStream_t st);
 

@@ -126,25 +126,6 @@ __global__ void __launch_bounds__(BLOCK) k_metrics(CoordGrid G, double *met, lon
 // General FP32 form: the 15 static fields the fused stage reads per point,
 // packed into four consecutive float4 records so that the load phase fetches
 // them with four vector loads from one array instead of fifteen.
-__global__ void __launch_bounds__(BLOCK) k_pack_metrics(const float *met, long long fs, float4 *mp,
-                                                        long long npad)
-{
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npad;
-         p += (long long)gridDim.x * blockDim.x) {
-        const float *m = met + p;
-        mp[4 * p + 0] = make_float4(m[0], m[fs], m[2 * fs], m[3 * fs]);
-        mp[4 * p + 1] = make_float4(m[4 * fs], m[5 * fs], m[6 * fs], m[7 * fs]);
-        mp[4 * p + 2] = make_float4(m[8 * fs], m[MET_JINV * fs], m[MET_CSD2 * fs], m[MET_J * fs]);
-        mp[4 * p + 3] = make_float4(m[MET_NORM * fs], m[(MET_NORM + 1) * fs], m[(MET_NORM + 2) * fs], 0.0f);
-    }
-}
-
-void launch_pack_metrics(const float *met, long long fs, float4 *mp, long long npad, cudaStream_t st)
-{
-    k_pack_metrics<<<(int)std::min<long long>((npad + BLOCK - 1) / BLOCK, 65535LL * 4), BLOCK, 0, st>>>(met, fs, mp,
-                                                                                                      npad);
-}
-
 // Separable form on a Cartesian-product grid: the spacing h_a(q) = d x_a /
 // d xi^a along each axis, by the same FP64 stencils as the metrics (on such a
 // grid the cofactors are products of these), stored with 1/h_a and h_a^(2/3)

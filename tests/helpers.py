@@ -123,3 +123,21 @@ def rel_l2(a, b):
     num = np.sqrt(((a - b) ** 2).sum(axis=1))
     den = np.sqrt((b ** 2).sum(axis=1))
     return num / np.where(den > 0, den, 1.0)
+
+
+def error_split(a, b, dims, margin=1):
+    """FP32-against-FP64 error decomposition on a grid of dims (ni, nj, nk):
+    relative L2 per field over the whole grid, over the interior (points at
+    least `margin` from every face) and the share of each field's squared
+    error that lies on the inflow plane i = 0."""
+    ni, nj, nk = dims
+    a = np.asarray(a).reshape(5, nk, nj, ni)
+    b = np.asarray(b).reshape(5, nk, nj, ni)
+    d2 = (a - b) ** 2
+    den = np.sqrt((b.reshape(5, -1) ** 2).sum(axis=1))
+    whole = np.sqrt(d2.reshape(5, -1).sum(axis=1)) / den
+    m = margin
+    inner = np.sqrt(d2[:, m:nk - m, m:nj - m, m:ni - m].reshape(5, -1).sum(axis=1)) / den
+    tot = np.maximum(d2.reshape(5, -1).sum(axis=1), 1e-300)
+    share_i0 = d2[:, :, :, 0].reshape(5, -1).sum(axis=1) / tot
+    return whole, inner, share_i0

@@ -64,7 +64,7 @@ def test_paper_scale_fp64_sampled_residual():
 
 
 def test_large_fp32_sampled_residual():
-    _check(I.jet_large, les.LES_FP32, 2e-4, 3000)
+    _check(I.jet_large, les.LES_FP32, 2e-5, 3000)
 
 
 def test_paper_scale_fp32_vs_fp64_100_steps():
@@ -81,4 +81,4 @@ def test_paper_scale_fp32_vs_fp64_100_steps():
         s.close()
     err = rel_l2(out[les.LES_FP32], out[les.LES_FP64])
     print("paper-scale fp32 vs fp64, 100 steps, rel L2 per field:", err)
-    assert np.all(err[[0, 1, 4]] <= 1e-5) and np.all(err <= 5e-5), err
+    assert np.all(err <= 1e-5), err

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import rel_l2, to_oracle
+from helpers import error_split, rel_l2, to_oracle
 from paper_2212_12365_gb300 import inputs as I
 from paper_2212_12365_gb300 import les
 
@@ -105,11 +105,18 @@ def test_paper_scale_fp32_error_100_and_1000_steps(fp64_run):
     d = (q - out["q1000"]).reshape(5, nk, nj, ni)[:, 8:-8, 8:-8, 8:-8]
     den = np.sqrt((out["q1000"] ** 2).sum(axis=1))
     ein = np.sqrt((d.reshape(5, -1) ** 2).sum(axis=1)) / den
-    print("fp32 vs fp64 rel L2 per field, 100 steps:", e100, " 1000 steps:", e1000, " interior:", ein)
+    share = error_split(q, out["q1000"], spec.dims)[2]
+    print("fp32 vs fp64 rel L2 per field, 100 steps:", e100, " 1000 steps:", e1000, " interior:", ein,
+          " i=0 share:", share)
     assert np.all(np.isfinite(q))
     assert np.all(e100 <= 1e-5), e100
-    assert np.all(e1000 <= 1e-3), e1000
     assert np.all(ein <= 1e-5), ein
+    # over the whole grid: rho, rho u, e at the bar; the transverse momenta
+    # may exceed it only by the inflow plane's far-field branch (see
+    # test_batched_fp32_against_oracle), which must then hold the excess
+    assert np.all(e1000[[0, 1, 4]] <= 1e-5), e1000
+    for f in (2, 3):
+        assert e1000[f] <= 1e-5 or (e1000[f] <= 2e-4 and share[f] >= 0.9), (f, e1000, share)
 
 
 def test_large_fp32_500_steps_with_probe():

@@ -34,7 +34,7 @@ def _oracle_state(spec, fp, prim):
     return g, p, m, q
 
 
-@pytest.mark.parametrize("prec,tol", [(les.LES_FP64, 1e-12), (les.LES_FP32, 2e-4)])
+@pytest.mark.parametrize("prec,tol", [(les.LES_FP64, 1e-12), (les.LES_FP32, 2e-5)])
 def test_polar_residual_parity(prec, tol):
     spec, fp = _polar((37, 15, 20))
     prim = I.smooth_random_primitives(spec, 21, amp=0.06)
@@ -83,7 +83,7 @@ def test_polar_jet_100_steps_fp32():
     err = rel_l2(s.get_state(les.LES_STATE_CONSERVED), ref)
     s.close()
     print("polar jet fp32 100 steps rel L2 per field:", err)
-    assert np.all(err[[0, 1, 4]] <= 1e-5) and np.all(err <= 5e-5), err
+    assert np.all(err <= 1e-5), err
 
 
 @pytest.mark.parametrize("prec", [les.LES_FP64, les.LES_FP32])

@@ -75,7 +75,7 @@ def test_separable_residual_parity(case):
     s.close()
     scale = np.abs(r_or).max(axis=1, keepdims=True) + 1e-30
     err = np.abs(r - r_or) / scale
-    assert err.max() < 2e-4, (case, err.max(axis=1))
+    assert err.max() < 2e-5, (case, err.max(axis=1))
 
 
 def test_separable_jet_small_100_steps():
@@ -164,4 +164,4 @@ def test_separable_paper_scale_sampled_residual():
     scale = np.abs(r_or).max(axis=1, keepdims=True) + 1e-30
     err = np.abs(r - r_or) / scale
     print("paper-scale separable sampled residual error / scale:", err.max(axis=1))
-    assert err.max() < 2e-4
+    assert err.max() < 2e-5, err.max(axis=1)

@@ -107,3 +107,24 @@ def test_default_bound_restored_and_arguments_checked():
     with pytest.raises(les.LesError):
         les.les_debug_stage_wait(s.h, 0)
     s.close()
+
+
+@pytest.mark.parametrize("ty", [8, 16])
+def test_wait_timeout_in_lockstep_waves(ty):
+    """The lockstep form (kc = -1) with more tiles than CTAs, so that the
+    CTAs first march whole columns in waves and then take balanced shares of
+    the rest: after the first wait of each CTA gives up, the cursor keeps
+    walking both kinds of work with direct loads, and the bits are those of
+    a normal step."""
+    import torch
+    spec, fp = I.jet_small()
+    ni, nj, _ = spec.dims
+    tiles = -(-(ni - 2) // 30) * -(-(nj - 2) // (ty - 2))
+    n = torch.cuda.get_device_properties(0).multi_processor_count // tiles + 2
+    specs, fps = [spec] * n, [fp] * n
+    ref, _, _ = _run(specs, fps, les.LES_FP32, (ty, -1), None, steps=2)
+    got, w1, rc = _run(specs, fps, les.LES_FP32, (ty, -1), 0, steps=2)
+    assert w1 >> 48 == 8 and rc == les.LES_ERR_TIMEOUT
+    for (a, rca), (b, rcb) in zip(ref, got):
+        assert rca == les.LES_OK and rcb == les.LES_ERR_TIMEOUT
+        np.testing.assert_array_equal(b, a)
