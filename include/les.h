@@ -315,7 +315,7 @@ int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints
  * (DFMA); 1: FP32 fused multiply-add (FFMA); 2: paired FP32 fused multiply-add
  * (fma.rn.f32x2, two lanes per instruction).  Launches a short loop of
  * independent multiply-add chains on the legacy default stream (timed with
- * CUDA events, best of three after a warm-up; a few milliseconds) and writes
+ * CUDA events, best of five after a warm-up; tens of milliseconds) and writes
  * the achieved rate in TFLOP/s (FMA = 2 FLOP) to *tflops.  Synchronises the
  * device's default stream.  Errors: LES_ERR_ARG (null pointer, unknown kind),
  * LES_ERR_CUDA. */

@@ -75,7 +75,7 @@ extern "C" int les_measure_peak(int kind, double *tflops)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LES_ERR_CUDA;
     // FP64 runs at a small fraction of the FP32 rate: fewer rounds
-    const int iters = kind == 0 ? 64 : 2048;
+    const int iters = kind == 0 ? 512 : 2048;
     const int blocks = nsm * 8, threads = 256;
     double *sink = nullptr; // never written (the store's condition is false)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -86,7 +86,7 @@ extern "C" int les_measure_peak(int kind, double *tflops)
     }
     float best = 1e30f;
     int rc = LES_OK;
-    for (int rep = 0; rep < 4 && rc == LES_OK; ++rep) {
+    for (int rep = 0; rep < 6 && rc == LES_OK; ++rep) {
         cudaEventRecord(e0, nullptr);
         if (kind == 0) k_fma_probe<0><<<blocks, threads>>>(sink, iters, 1.0000001, 0.9999999);
         else if (kind == 1) k_fma_probe<1><<<blocks, threads>>>(sink, iters, 1.0000001, 0.9999999);

@@ -30,20 +30,36 @@ __constant__ double c_alpha[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
 
 // Reciprocal.  FP32 uses the hardware division.  In FP64, whose pipe is the
 // bottleneck on this GPU, the reciprocal is a Newton-Raphson iteration
-// r <- r (2 - b r) from a single-precision seed: each step squares the
-// relative error of the 24-bit seed, so two steps reach double rounding (a
-// unit in the last place), at fewer FP64 operations than an IEEE division.
-// Arguments are positive normal numbers (densities, temperatures, sensor
-// denominators).  Square roots stay the native ones (an iteration from a
-// single-precision seed measured slower, and must special-case zero strain).
+// r <- r (2 - b r) from the hardware's approximate FP64 reciprocal (a seed of
+// about single precision, taken without converting through FP32): each step
+// squares the relative error, so two steps reach double rounding (a unit in
+// the last place) at fewer FP64 operations than an IEEE division, and one
+// step leaves a relative error near 1e-14, which is all a factor needs whose
+// own error enters the residual damped by its small weight (pressure sensor,
+// Sutherland law).  Arguments are positive normal numbers (densities,
+// temperatures, sensor denominators).  Square roots stay the native ones (an
+// iteration from a single-precision seed measured slower, and must
+// special-case zero strain).
+__device__ __forceinline__ double rcp_seed(double b)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+    return r;
+}
 template <typename real> __device__ __forceinline__ real rcp_(real b) { return real(1) / b; }
 template <> __device__ __forceinline__ double rcp_<double>(double b)
 {
-    double r = (double)__frcp_rn((float)b);
+    double r = rcp_seed(b);
     double e = fma(-b, r, 1.0);
     r = fma(r, e, r);
     e = fma(-b, r, 1.0);
     return fma(r, e, r);
+}
+template <typename real> __device__ __forceinline__ real rcp1_(real b) { return real(1) / b; }
+template <> __device__ __forceinline__ double rcp1_<double>(double b)
+{
+    const double r = rcp_seed(b);
+    return fma(r, fma(-b, r, 1.0), r);
 }
 
 // ---------------------------------------------------------------------------
@@ -78,21 +94,25 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
         const real T = gam * p * rrho;
         const real sT = sqrt(T); // speed of sound: c^2 = gamma p / rho = T in jet units
         const real S = (real)J.suth_S;
-        const real mu = T * sT * (real(1) + S) * rcp_<real>(T + S);
+        const real mu = T * sT * (real(1) + S) * rcp1_<real>(T + S);
         const real rH = e + p;
         real lam[3];
+        const real hp = real(0.5) * p;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const real mx = M[(3 * a) * fs + lp], my = M[(3 * a + 1) * fs + lp],
                        mz = M[(3 * a + 2) * fs + lp];
             const real JU = mx * u + my * v + mz * w; // J^-1 times the contravariant velocity
             lam[a] = (fabs(JU) + sT * M[(MET_NORM + a) * fs + lp]) * rj;
+            // half the inviscid point flux: the interface average is the sum
+            // of the two points' halves
+            const real hJU = real(0.5) * JU;
             real *F = P + (P_F0 + 5 * a) * fs + lp;
-            F[0] = rho * JU;
-            F[fs] = ru * JU + p * mx;
-            F[2 * fs] = rv * JU + p * my;
-            F[3 * fs] = rw * JU + p * mz;
-            F[4 * fs] = rH * JU;
+            F[0] = rho * hJU;
+            F[fs] = ru * hJU + hp * mx;
+            F[2 * fs] = rv * hJU + hp * my;
+            F[3 * fs] = rw * hJU + hp * mz;
+            F[4 * fs] = rH * hJU;
         }
         // lambda_a + (lambda_a lambda_b)^1/2 + (lambda_a lambda_d)^1/2 = s_a (s_a + s_b + s_d)
         const real sq0 = sqrt(lam[0]), sq1 = sqrt(lam[1]), sq2 = sqrt(lam[2]);
@@ -161,7 +181,7 @@ __global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict_
             const real pm = P[P_P * fs + lidx(J, rm[0], rm[1], rm[2])];
             const real p0 = P[P_P * fs + lidx(J, r0[0], r0[1], r0[2])];
             const real pp = P[P_P * fs + lidx(J, rp[0], rp[1], rp[2])];
-            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) * rcp_<real>(pp + real(2) * p0 + pm);
+            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) * rcp1_<real>(pp + real(2) * p0 + pm);
         }
 #pragma unroll
         for (int f = 0; f < 4; ++f)
@@ -235,21 +255,23 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     const real eps4 = fmax(real(0), (real)J.k4 - eps2);
     const real jb = M[(MET_JB + a) * fs + L];
     const real sc = jb * real(0.5) * (P[(P_LXI + a) * fs + L] + P[(P_LXI + a) * fs + R]);
-    const real se2 = sc * eps2, se4 = sc * eps4;
+    const real se4 = sc * eps4;
+    // se2 dW - se4 (dW(+3/2) - 2 dW(+1/2) + dW(-1/2)) with the third
+    // difference written as W(R+1) - W(L-1) - 3 dW(+1/2): the flux gains
+    // se4 (W(R+1) - W(L-1)) + (se2 + 3 se4) (W(L) - W(R))
+    const real c2 = fma(real(3), se4, sc * eps2);
     const int wf[5] = {P_RHO, P_RU, P_RV, P_RW, P_RH};
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
         const real *W = P + wf[f] * fs;
         const real wL = W[L], wR = W[R];
-        const real dW0 = wR - wL;
-        // third difference dW(+3/2) - 2 dW(+1/2) + dW(-1/2) = W(R+1) - W(L-1) - 3 dW(+1/2);
         // the mirrored difference at a non-periodic end, dW(outside) = -dW(+1/2),
         // is the missing point W(R+1) = W(L) (resp. W(L-1) = W(R))
         const real wRp = hi_end ? wL : W[Rp];
         const real wLm = lo_end ? wR : W[Lm];
-        const real d3 = (wRp - wLm) - real(3) * dW0;
         const real *F = P + (P_F0 + 5 * a + f) * fs;
-        H[f] = real(0.5) * (F[L] + F[R]) + (se4 * d3 - se2 * dW0);
+        // centred flux: the sum of the two points' stored half fluxes
+        H[f] = fma(c2, wL - wR, fma(se4, wRp - wLm, F[L] + F[R]));
     }
     // compact viscous + SGS flux: normal derivative from the two points,
     // tangential derivatives averaged, coefficients/metrics/velocity averaged.
