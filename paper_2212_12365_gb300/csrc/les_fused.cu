@@ -85,6 +85,8 @@ __device__ __forceinline__ float2 sqrt2(float2 x)
 //                             (m4 m5) (m6 m7) (m8 J^-1), streamed in by
 //                             cp.async one plane ahead (general form only)
 //   SH [5][NT] float          eta flux of each thread's second row
+//   QZ [5][TY-2][30] float    Q(0) of the tile's updated points, copied in
+//                             by cp.async during the plane's iteration
 //   HX [C2], HY [TY+4] float4 separable form: (h, 1/h, h^(2/3), 0) of the
 //                             tile's columns / rows
 //   QG [5][TY+4][40] float    the next plane's state box (TMA), 128-aligned,
@@ -111,7 +113,9 @@ template <int TY, bool SEP> struct Geo {
     static constexpr size_t O_GC = O_GD + 16ull * 2 * 6 * N1;
     static constexpr size_t O_MA = O_GC + 16ull * 2 * 4 * N1;
     static constexpr size_t O_SH = O_MA + (SEP ? 0ull : 16ull * 3 * 5 * N1);
-    static constexpr size_t O_HX = O_SH + 4ull * 5 * NT;
+    static constexpr int QZN = (TY - 2) * (FX - 2); // updated points of a tile plane
+    static constexpr size_t O_QZ = O_SH + 4ull * 5 * NT;
+    static constexpr size_t O_HX = (O_QZ + 4ull * 5 * QZN + 15) / 16 * 16;
     static constexpr size_t O_HY = O_HX + 16ull * C2;
     static constexpr size_t O_QG = (O_HY + 16ull * BR + 127) / 128 * 128;
     static constexpr unsigned BOX_BYTES = 4u * 5 * BR * TMA_BOX_X;
@@ -125,7 +129,7 @@ template <int TY, bool SEP> struct Sm {
     float4 *PA, *PB, *PC;
     float2 *PH;
     float4 *GD, *GC, *MA;
-    float *SH;
+    float *SH, *QZ;
     float4 *HX, *HY;
     float *QG;
     unsigned long long *MBAR;
@@ -134,6 +138,7 @@ template <int TY, bool SEP> struct Sm {
           PC((float4 *)(b + Geo<TY, SEP>::O_PC)), PH((float2 *)(b + Geo<TY, SEP>::O_PH)),
           GD((float4 *)(b + Geo<TY, SEP>::O_GD)), GC((float4 *)(b + Geo<TY, SEP>::O_GC)),
           MA((float4 *)(b + Geo<TY, SEP>::O_MA)), SH((float *)(b + Geo<TY, SEP>::O_SH)),
+          QZ((float *)(b + Geo<TY, SEP>::O_QZ)),
           HX((float4 *)(b + Geo<TY, SEP>::O_HX)), HY((float4 *)(b + Geo<TY, SEP>::O_HY)),
           QG((float *)(b + Geo<TY, SEP>::O_QG)), MBAR((unsigned long long *)(b + Geo<TY, SEP>::O_MBAR))
     {
@@ -153,17 +158,14 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32_(dst)), "l"(src) : "memory");
 }
+// 4-byte variant (scattered Q(0) values)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32_(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// Global load issued where it stands in the program (not moved towards its
-// use), not kept in L1: Q(0) of the update, needed only after the interfaces.
-__device__ __forceinline__ float ld_early(const float *p)
-{
-    float v;
-    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
 
 // Index of a tile cell along an axis: wrapped on a periodic axis; on a
 // non-periodic one the mirror image about the end point (-g, 2(n-1) - g),
@@ -563,6 +565,8 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         const bool outA = col_out && rA >= 1 && rA <= TY - 2 && (jb + rA) < jhi;
         const bool outB = col_out && rB >= 1 && rB <= TY - 2 && (jb + rB) < jhi;
         const long long ocolA = (long long)gjA * J.pitch + gi, ocolB = (long long)gjB * J.pitch + gi;
+        // slots of the two rows' Q(0) values in QZ (outputs only)
+        const int zA = (rA - 1) * (FX - 2) + (tx - 1), zB = (rB - 1) * (FX - 2) + (tx - 1);
         // the R2 pair cells this thread loads (at most two) and, per row, the
         // offset of its source point in the staging box and in a plane
         int lc[2];
@@ -943,12 +947,28 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             if (tma_off) tmap = nullptr;
             // the next plane's box, in flight during the rest of this iteration
             if (tmap && kL < klast && !(!pk && kL + 1 == nk)) stage_box(kL + 1);
-            // the metrics of the next gradient plane (kL), in flight until the
-            // next iteration; one copy group per iteration
+            // one copy group per iteration: the metrics of the next gradient
+            // plane (kL), waited for in the next iteration, and Q(0) of this
+            // iteration's updated points (plane kL - 2), waited for before
+            // the update; each thread copies, and later reads, its own values
             if constexpr (!SEP) {
                 if (kL >= k0 - 1 && kL <= k1) fetch_met(kL);
-                cp_async_commit();
             }
+            if (!rhs_only && kL - 2 >= k0 && kL - 2 <= k1 - 1) {
+                const long long pU = (long long)map_idx(kL - 2, nk, pk) * plane;
+                const float *Q0 = J.q[0];
+                if (outA) {
+                    const long long oA = CK_G(4, pU + ocolA, J.npts_pad);
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) cp_async4(S.QZ + CK_TAB(f * G_::QZN + zA, 5 * G_::QZN), Q0 + f * fs + oA);
+                }
+                if (outB) {
+                    const long long oB = CK_G(4, pU + ocolB, J.npts_pad);
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) cp_async4(S.QZ + CK_TAB(f * G_::QZN + zB, 5 * G_::QZN), Q0 + f * fs + oB);
+                }
+            }
+            cp_async_commit();
             // W of the own column at plane k0 - 2: the outer point of the
             // chunk's first zeta interface
             if (kL == k0) wof(CK_RING(rslot<NRING>(kL - 2) * N2 + c2), Wc);
@@ -988,27 +1008,9 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     hy[f] = bc(0.0f);
                     hz[f] = bc(0.0f);
                 }
-                // Q(0) of the updated points, requested early
                 const bool updA = !first && outA && kU >= k0, updB = !first && outB && kU >= k0;
                 const long long pU = (long long)gkU * plane;
                 const long long oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
-                float q0A[5], q0B[5];
-#pragma unroll
-                for (int f = 0; f < 5; ++f) {
-                    q0A[f] = 0.0f;
-                    q0B[f] = 0.0f;
-                }
-                if (!rhs_only) {
-                    const float *Q0 = J.q[0];
-                    if (updA) {
-#pragma unroll
-                        for (int f = 0; f < 5; ++f) q0A[f] = ld_early(Q0 + f * fs + oA);
-                    }
-                    if (updB) {
-#pragma unroll
-                        for (int f = 0; f < 5; ++f) q0B[f] = ld_early(Q0 + f * fs + oB);
-                    }
-                }
                 if (!first) {
                     // xi: R = the next column (lanes 0..30; lane 31's R has no R1 data)
                     if (tx <= FX - 2) {
@@ -1114,6 +1116,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 }
                 __syncthreads(); // eta fluxes of the row below; the first plane's read of W below
                 if (updA || updB) {
+                    cp_async_wait_all(); // this thread's Q(0) copies
                     // residual R = sum over axes of flux(+1/2) - flux(-1/2); the
                     // -1/2 zeta flux from the previous plane, the -1/2 eta flux
                     // of the first row from the thread row below and of the
@@ -1139,11 +1142,13 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                         const float2 adtj = mul2(bc(adt), rjU);
                         if (updA) {
 #pragma unroll
-                            for (int f = 0; f < 5; ++f) Qd[f * fs + oA] = fmaf(-adtj.x, Rs[f].x, q0A[f]);
+                            for (int f = 0; f < 5; ++f)
+                                Qd[f * fs + oA] = fmaf(-adtj.x, Rs[f].x, S.QZ[CK_TAB(f * G_::QZN + zA, 5 * G_::QZN)]);
                         }
                         if (updB) {
 #pragma unroll
-                            for (int f = 0; f < 5; ++f) Qd[f * fs + oB] = fmaf(-adtj.y, Rs[f].y, q0B[f]);
+                            for (int f = 0; f < 5; ++f)
+                                Qd[f * fs + oB] = fmaf(-adtj.y, Rs[f].y, S.QZ[CK_TAB(f * G_::QZN + zB, 5 * G_::QZN)]);
                         }
                     }
                 }
@@ -1159,7 +1164,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             rjU = rjG; // plane kG is the next iteration's kU
         }
     }
-    if constexpr (!SEP) cp_async_wait_all();
+    cp_async_wait_all();
     // a copy whose wait gave up may still be in flight into this CTA's
     // shared memory: its issuer waits for it (bounded) before exiting; if
     // that wait gives up too, the copy may land in the shared memory of the
