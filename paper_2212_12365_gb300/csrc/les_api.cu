@@ -81,7 +81,8 @@ struct les_handle {
     cudaGraphExec_t gexec = nullptr;
     // fused FP32 stage: work-list tables (all jets; and one per jet with item0 = 0)
     FusedJet *d_fj = nullptr, *d_fj1 = nullptr;
-    std::vector<FusedJet> fj;
+    std::vector<FusedJet> fj, fj1; // host copies of d_fj and d_fj1
+    std::vector<JetDev<float>> jd32; // host copy of the FP32 jet table
     int fused_ty = 16;
     int fused_balanced = 0; // 0: k-chunk items, 1: balanced ranges, 2: lockstep waves, then balanced ranges
     int fused_items = 0, fused_tiles = 0;
@@ -447,6 +448,7 @@ static int set_fused_tiling(les_handle *h, int ty, int kc)
     CK(cudaMemcpyAsync(h->d_fj, h->fj.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_fj1, one.data(), sizeof(FusedJet) * h->njets, cudaMemcpyHostToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
+    h->fj1 = one;
     return LES_OK;
 }
 
@@ -468,12 +470,15 @@ static void fused_launch(les_handle *h, int jet, int src, int dst, int stage, in
     const int grid = std::max(1, std::min(items, h->nsm * h->fused_cps[h->fused_ty == 16 ? 1 : 0]));
     if (jet >= 0) jets += jet;
     const int bal = h->fused_balanced;
+    // a single jet's table entries travel as kernel parameters
+    const JetDev<float> *j1 = nj == 1 ? &h->jd32[jet < 0 ? 0 : jet] : nullptr;
+    const FusedJet *f1 = nj == 1 ? (jet < 0 ? &h->fj[0] : &h->fj1[jet]) : nullptr;
     if (h->fused_ty == 16)
         launch_fused<16>(jets, fj, nj, items, tiles, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
-                         h->stage_wait_limit, st);
+                         h->stage_wait_limit, j1, f1, st);
     else
         launch_fused<8>(jets, fj, nj, items, tiles, grid, src, dst, stage, h->d_dt, rhs_only, h->sep, bal,
-                         h->stage_wait_limit, st);
+                         h->stage_wait_limit, j1, f1, st);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the
@@ -619,6 +624,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
     std::vector<JetDev<real>> D(njets);
     for (int j = 0; j < njets; ++j) fill_jetdev<real>(h, h->J[j], D[j]);
     CK(cudaMemcpyAsync(h->d_jets, D.data(), sizeof(JetDev<real>) * njets, cudaMemcpyHostToDevice, h->st));
+    if constexpr (sizeof(real) == sizeof(float)) h->jd32 = D;
     if (h->prec == LES_FP32) {
         if (fused_prepare<16>() != 0 || fused_prepare<8>() != 0)
             return bail(fail(h, LES_ERR_CUDA, "fused kernel shared-memory attribute"));

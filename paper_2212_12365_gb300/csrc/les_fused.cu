@@ -89,6 +89,8 @@ __device__ __forceinline__ float2 sqrt2(float2 x)
 //                             by cp.async during the plane's iteration
 //   HX [C2], HY [TY+4] float4 separable form: (h, 1/h, h^(2/3), 0) of the
 //                             tile's columns / rows
+//   HZ [4] float4             separable form: the same for planes k (slot k & 3),
+//                             copied in two planes ahead
 //   QG [5][TY+4][40] float    the next plane's state box (TMA), 128-aligned,
 //                             then its mbarrier
 // A "pair cell" is one column of two rows (2p, 2p+1); its float4 records
@@ -117,7 +119,8 @@ template <int TY, bool SEP> struct Geo {
     static constexpr size_t O_QZ = O_SH + 4ull * 5 * NT;
     static constexpr size_t O_HX = (O_QZ + 4ull * 5 * QZN + 15) / 16 * 16;
     static constexpr size_t O_HY = O_HX + 16ull * C2;
-    static constexpr size_t O_QG = (O_HY + 16ull * BR + 127) / 128 * 128;
+    static constexpr size_t O_HZ = O_HY + 16ull * BR;
+    static constexpr size_t O_QG = (O_HZ + 16ull * 4 + 127) / 128 * 128;
     static constexpr unsigned BOX_BYTES = 4u * 5 * BR * TMA_BOX_X;
     static_assert(BOX_BYTES % 16 == 0, "box size");
     static constexpr size_t O_MBAR = O_QG + BOX_BYTES;
@@ -130,7 +133,7 @@ template <int TY, bool SEP> struct Sm {
     float2 *PH;
     float4 *GD, *GC, *MA;
     float *SH, *QZ;
-    float4 *HX, *HY;
+    float4 *HX, *HY, *HZ;
     float *QG;
     unsigned long long *MBAR;
     __device__ __forceinline__ explicit Sm(unsigned char *b)
@@ -140,6 +143,7 @@ template <int TY, bool SEP> struct Sm {
           MA((float4 *)(b + Geo<TY, SEP>::O_MA)), SH((float *)(b + Geo<TY, SEP>::O_SH)),
           QZ((float *)(b + Geo<TY, SEP>::O_QZ)),
           HX((float4 *)(b + Geo<TY, SEP>::O_HX)), HY((float4 *)(b + Geo<TY, SEP>::O_HY)),
+          HZ((float4 *)(b + Geo<TY, SEP>::O_HZ)),
           QG((float *)(b + Geo<TY, SEP>::O_QG)), MBAR((unsigned long long *)(b + Geo<TY, SEP>::O_MBAR))
     {
     }
@@ -419,11 +423,22 @@ __device__ __forceinline__ void iface_sep(const FusedParams &FP, const Pts &L, c
 #define CK_TAB(x, n) ((int)LES_BOUNDS(J.oob, 6, (x), (n)))
 #define CK_SH(x) ((int)LES_BOUNDS(J.oob, 7, (x), 5 * NT))
 
-template <int TY, bool SEP>
+// The jet's table entries: in the single-jet form (ONE) the kernel
+// parameters, whose fields the compiler reads from the parameter bank
+// (warp-uniform operands, no memory loads in the plane loop); else the
+// device tables.
+template <bool ONE, typename T> __device__ __forceinline__ const T &jet_entry(const T &one, const T *tab, int j)
+{
+    if constexpr (ONE) return one;
+    else return tab[j];
+}
+
+template <int TY, bool SEP, bool ONE>
 __global__ void __launch_bounds__(FX * TY / 2, 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
             int total_items, int total_tiles, int src, int dst, int stage, const double *__restrict__ dt,
-            int rhs_only, int balanced, int wait_limit)
+            int rhs_only, int balanced, int wait_limit, const __grid_constant__ JetDev<float> j1,
+            const __grid_constant__ FusedJet f1)
 {
     using G_ = Geo<TY, SEP>;
     constexpr int TR = G_::TR, NT = G_::NT, C2 = G_::C2, N2 = G_::N2, N1 = G_::N1, BR = G_::BR;
@@ -462,6 +477,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
     const int nwave = balanced == 2 ? total_tiles / (int)gridDim.x : 0;
     int wave = 0;
     auto jet_of_tile = [&](int t) {
+        if constexpr (ONE) return 0;
         int lo = 0, hi = njets;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -473,14 +489,14 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         while (wave <= nwave) {
             if (wave < nwave) {
                 const int t = blockIdx.x + wave * gridDim.x;
-                const FusedJet &Fw = fj[jet_of_tile(t)];
+                const FusedJet &Fw = jet_entry<ONE>(f1, fj, jet_of_tile(t));
                 w = Fw.item0 + (t - Fw.tile0) * Fw.nkc;
                 wend = w + Fw.nkc;
             } else {
                 const int t1 = nwave * gridDim.x;
                 int i1 = total_items;
                 if (t1 < total_tiles) {
-                    const FusedJet &Fw = fj[jet_of_tile(t1)];
+                    const FusedJet &Fw = jet_entry<ONE>(f1, fj, jet_of_tile(t1));
                     i1 = Fw.item0 + (t1 - Fw.tile0) * Fw.nkc;
                 }
                 const long long rem = total_items - i1;
@@ -496,7 +512,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
     while (balanced ? (w < wend || next_range()) : item < total_items) {
         const int key = balanced ? w : item;
         int jet = 0;
-        {
+        if constexpr (!ONE) {
             int lo = 0, hi = njets;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
@@ -504,8 +520,8 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             }
             jet = lo;
         }
-        const JetDev<float> &J = jets[jet];
-        const FusedJet &F = fj[jet];
+        const JetDev<float> &J = jet_entry<ONE>(j1, jets, jet);
+        const FusedJet &F = jet_entry<ONE>(f1, fj, jet);
         const FusedParams &FP = F.fp;
         const int ni = J.n[0], nj = J.n[1], nk = J.n[2];
         const int pi = J.per[0], pj = J.per[1], pk = J.per[2];
@@ -765,7 +781,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 // diagonal cofactors: 1/h_a per axis; J = prod 1/h_a
                 const float4 hX = S.HX[tx + 1];
                 const float4 hYA = S.HY[rA + 2], hYB = S.HY[rB + 2];
-                const float4 hZ = F.h1[2][gk];
+                const float4 hZ = S.HZ[kg & 3];
                 rh[0] = bc(hX.y);
                 rh[1] = f2(hYA.y, hYB.y);
                 rh[2] = bc(hZ.y);
@@ -941,6 +957,9 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     S.PH[cell] = add2(e, p);
                 }
             }
+            // separable form: thread 0's spacing copy of plane kL - 1 (issued
+            // two iterations ago) has landed, and the barrier publishes it
+            if (SEP && tid == 0) cp_async_wait_prev();
             // (a thread whose staging wait gave up turns staging off for the
             // whole CTA here)
             tma_off = __syncthreads_or(tma_off) != 0;
@@ -953,6 +972,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             // the update; each thread copies, and later reads, its own values
             if constexpr (!SEP) {
                 if (kL >= k0 - 1 && kL <= k1) fetch_met(kL);
+            } else {
+                // the spacings of plane kL + 1 into the slot of plane kL - 3,
+                // whose last reads preceded the barrier above
+                if (tid == 0) cp_async16(S.HZ + ((kL + 1) & 3), F.h1[2] + map_idx(kL + 1, nk, pk));
             }
             if (!rhs_only && kL - 2 >= k0 && kL - 2 <= k1 - 1) {
                 const long long pU = (long long)map_idx(kL - 2, nk, pk) * plane;
@@ -995,8 +1018,8 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 if constexpr (SEP) {
                     hXo = S.HX[tx + 1];
                     hXp = S.HX[tx + 2];
-                    hZo = F.h1[2][gkU];
-                    hZp = F.h1[2][map_idx(kU + 1, nk, pk)];
+                    hZo = S.HZ[kU & 3];
+                    hZp = S.HZ[(kU + 1) & 3];
                     const float4 yA = S.HY[rA + 2], yB = S.HY[rB + 2];
                     hYo = f2(yA.x, yB.x);
                     rhYo = f2(yA.y, yB.y);
@@ -1171,7 +1194,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
     // next CTA on this SM, which is recorded as site 9 (it outranks site 8:
     // the state can no longer be trusted)
     if (pend && tid == 0 && !mbar_wait(S.MBAR, tpar, MBAR_WAIT_LIMIT)) {
-        const JetDev<float> &J0 = jets[0];
+        const JetDev<float> &J0 = jet_entry<ONE>(j1, jets, 0);
         if (J0.oob) atomicMax(J0.oob, 9ull << 48);
     }
 }
@@ -1225,11 +1248,15 @@ void launch_pack_pairs(const float *met, long long fs, int pitch, int nj, int nk
 
 template <int TY> int fused_prepare()
 {
-    int rc = (int)cudaFuncSetAttribute(k_fused<TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    int rc = (int)cudaFuncSetAttribute(k_fused<TY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Geo<TY, false>::BYTES);
-    if (rc) return rc;
-    return (int)cudaFuncSetAttribute(k_fused<TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Geo<TY, true>::BYTES);
+    if (!rc) rc = (int)cudaFuncSetAttribute(k_fused<TY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)Geo<TY, true>::BYTES);
+    if (!rc) rc = (int)cudaFuncSetAttribute(k_fused<TY, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)Geo<TY, false>::BYTES);
+    if (!rc) rc = (int)cudaFuncSetAttribute(k_fused<TY, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)Geo<TY, true>::BYTES);
+    return rc;
 }
 
 int fused_ctas_per_sm(int ty, int separable)
@@ -1237,14 +1264,14 @@ int fused_ctas_per_sm(int ty, int separable)
     int n = 0;
     cudaError_t e;
     if (ty == 16)
-        e = separable ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<16, true>, FX * 8,
+        e = separable ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<16, true, true>, FX * 8,
                                                                       Geo<16, true>::BYTES)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<16, false>, FX * 8,
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<16, false, true>, FX * 8,
                                                                       Geo<16, false>::BYTES);
     else
-        e = separable ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<8, true>, FX * 4,
+        e = separable ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<8, true, true>, FX * 4,
                                                                       Geo<8, true>::BYTES)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<8, false>, FX * 4,
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<8, false, true>, FX * 4,
                                                                       Geo<8, false>::BYTES);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1256,24 +1283,39 @@ int fused_ctas_per_sm(int ty, int separable)
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int total_tiles,
                   int grid, int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
-                  int wait_limit, cudaStream_t st)
+                  int wait_limit, const JetDev<float> *j1, const FusedJet *f1, cudaStream_t st)
 {
     dim3 block(FX, TY / 2);
     if (wait_limit < 0) wait_limit = MBAR_WAIT_LIMIT;
-    if (separable)
-        k_fused<TY, true><<<grid, block, Geo<TY, true>::BYTES, st>>>(jets, fj, njets, total_items, total_tiles, src,
-                                                                    dst, stage, dt, rhs_only, balanced, wait_limit);
-    else
-        k_fused<TY, false><<<grid, block, Geo<TY, false>::BYTES, st>>>(jets, fj, njets, total_items, total_tiles,
-                                                                      src, dst, stage, dt, rhs_only, balanced,
-                                                                      wait_limit);
+    const bool one = njets == 1 && j1 && f1;
+    JetDev<float> jz{};
+    FusedJet fz{};
+    const JetDev<float> &ja = one ? *j1 : jz;
+    const FusedJet &fa = one ? *f1 : fz;
+    if (separable) {
+        if (one)
+            k_fused<TY, true, true><<<grid, block, Geo<TY, true>::BYTES, st>>>(
+                jets, fj, njets, total_items, total_tiles, src, dst, stage, dt, rhs_only, balanced, wait_limit, ja, fa);
+        else
+            k_fused<TY, true, false><<<grid, block, Geo<TY, true>::BYTES, st>>>(
+                jets, fj, njets, total_items, total_tiles, src, dst, stage, dt, rhs_only, balanced, wait_limit, ja, fa);
+    } else {
+        if (one)
+            k_fused<TY, false, true><<<grid, block, Geo<TY, false>::BYTES, st>>>(
+                jets, fj, njets, total_items, total_tiles, src, dst, stage, dt, rhs_only, balanced, wait_limit, ja, fa);
+        else
+            k_fused<TY, false, false><<<grid, block, Geo<TY, false>::BYTES, st>>>(
+                jets, fj, njets, total_items, total_tiles, src, dst, stage, dt, rhs_only, balanced, wait_limit, ja, fa);
+    }
 }
 
 template int fused_prepare<16>();
 template int fused_prepare<8>();
 template void launch_fused<16>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int, int,
-                               const double *, int, int, int, int, cudaStream_t);
+                               const double *, int, int, int, int, const JetDev<float> *, const FusedJet *,
+                               cudaStream_t);
 template void launch_fused<8>(const JetDev<float> *, const FusedJet *, int, int, int, int, int, int, int,
-                              const double *, int, int, int, int, cudaStream_t);
+                              const double *, int, int, int, int, const JetDev<float> *, const FusedJet *,
+                              cudaStream_t);
 
 } // namespace les

@@ -274,10 +274,14 @@ template <int TY> int fused_prepare();
 // resident CTAs per SM of the fused stage for tile height ty (general or
 // separable form), from the occupancy calculator; 1 if it cannot tell
 int fused_ctas_per_sm(int ty, int separable);
+// One launch of the fused stage.  jets / fj: the device tables of the njets
+// jets; for a single jet (njets == 1) j1 / f1 are host copies of its two
+// entries, passed by value as kernel parameters, so that the kernel reads the
+// jet's constants from the parameter bank (null otherwise).
 template <int TY>
 void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int total_items, int total_tiles,
                   int grid, int src, int dst, int stage, const double *dt, int rhs_only, int separable, int balanced,
-                  int wait_limit, cudaStream_t st);
+                  int wait_limit, const JetDev<float> *j1, const FusedJet *f1, cudaStream_t st);
 
 // General FP32 form: the paired static records (see FusedJet::mp) from the
 // FP32 static fields; mp holds nk * ((nj + 1) / 2) * pitch * 8 float4.
