@@ -34,7 +34,7 @@ struct JetHost {
     char *met, *q[3], *prim, *grad, *hflux, *rhs;
     double *jinv64, *inflow_r;
     float4 *h1[3];                     // FP32: 1-D spacings of a product grid (separable form)
-    float4 *mp;                        // FP32 general form: paired static records (8 float4 / row pair)
+    float4 *mp;                        // FP32 general form: paired static records (5 float4 / row pair)
     int nblk_pt, nblk_bc[3];
 };
 
@@ -228,7 +228,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     size_t o_inr = take((size_t)g->nj * g->nk * 8);
     size_t o_h1 = prec == LES_FP32 ? take((size_t)(g->ni + g->nj + g->nk) * 16) : 0;
     const bool packed = g->precision == LES_FP32; // general FP32 form only
-    size_t o_mp = packed ? take((size_t)g->nk * ((g->nj + 1) / 2) * J.pitch * 128) : 0;
+    size_t o_mp = packed ? take((size_t)g->nk * ((g->nj + 1) / 2) * J.pitch * 80) : 0;
     J.bytes = off;
     // store offsets relative to the jet region in the pointers for now
     J.met = (char *)o_met;

@@ -116,11 +116,12 @@ template <int TY, bool SEP> struct Geo {
     static constexpr size_t O_MA = O_GC + 16ull * 2 * 4 * N1;
     static constexpr size_t O_SH = O_MA + (SEP ? 0ull : 16ull * 3 * 5 * N1);
     static constexpr int QZN = (TY - 2) * (FX - 2); // updated points of a tile plane
-    static constexpr size_t O_QZ = O_SH + 4ull * 5 * NT;
-    static constexpr size_t O_HX = (O_QZ + 4ull * 5 * QZN + 15) / 16 * 16;
-    static constexpr size_t O_HY = O_HX + 16ull * C2;
-    static constexpr size_t O_HZ = O_HY + 16ull * BR;
-    static constexpr size_t O_QG = (O_HZ + 16ull * 4 + 127) / 128 * 128;
+    static constexpr size_t O_QZ = (O_SH + 4ull * 5 * NT + 15) / 16 * 16;
+    static constexpr size_t O_HX = O_QZ + 4ull * 5 * QZN;
+    // (the spacing tables exist in the separable form only)
+    static constexpr size_t O_HY = O_HX + (SEP ? 16ull * C2 : 0ull);
+    static constexpr size_t O_HZ = O_HY + (SEP ? 16ull * BR : 0ull);
+    static constexpr size_t O_QG = (O_HZ + (SEP ? 16ull * 4 : 0ull) + 127) / 128 * 128;
     static constexpr unsigned BOX_BYTES = 4u * 5 * BR * TMA_BOX_X;
     static_assert(BOX_BYTES % 16 == 0, "box size");
     static constexpr size_t O_MBAR = O_QG + BOX_BYTES;
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         float *__restrict__ Qd = J.q[dst];
         const float adt = rhs_only ? 0.0f : c_alpha_f[stage] * (float)dt[jet];
         const float4 *__restrict__ mp = F.mp;
-        const long long nrec = (long long)nk * F.njp * J.pitch * 8;
+        const long long nrec = (long long)nk * F.njp * 5 * J.pitch;
         (void)nrec; // bound of the static-record checks of a LES_BOUNDS_CHECK build
 
         // ---- per-item setup ----
@@ -647,18 +648,25 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         auto fetch_met = [&](int kg) {
             const int gk = map_idx(kg, nk, pk);
             float4 *dst = S.MA + CK_TAB((r3(kg) * 5) * N1 + c1, 15 * N1);
+            const long long rp = J.pitch;
             if (!rec_split) {
-                const float4 *p = mp + CK_G(3, (((long long)gk * F.njp + jpA) * J.pitch + gi) * 8, nrec);
+                const long long r0 = ((long long)gk * F.njp + jpA) * 5 * rp + gi;
+                const float4 *p = mp + CK_G(3, r0, nrec);
+                (void)CK_G(3, r0 + 4 * rp, nrec);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) cp_async16(dst + q * N1, p + q);
+                for (int q = 0; q < 5; ++q) cp_async16(dst + q * N1, p + q * rp);
             } else {
                 // rows from two records: take each row's lane
-                const float4 *pa = mp + CK_G(3, (((long long)gk * F.njp + (gjA >> 1)) * J.pitch + gi) * 8, nrec);
-                const float4 *pb = mp + CK_G(3, (((long long)gk * F.njp + (gjB >> 1)) * J.pitch + gi) * 8, nrec);
+                const long long ra = ((long long)gk * F.njp + (gjA >> 1)) * 5 * rp + gi;
+                const long long rb = ((long long)gk * F.njp + (gjB >> 1)) * 5 * rp + gi;
+                const float4 *pa = mp + CK_G(3, ra, nrec);
+                const float4 *pb = mp + CK_G(3, rb, nrec);
+                (void)CK_G(3, ra + 4 * rp, nrec);
+                (void)CK_G(3, rb + 4 * rp, nrec);
                 const bool sa = gjA & 1, sb = gjB & 1;
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    const float4 a = pa[q], b = pb[q];
+                    const float4 a = pa[q * rp], b = pb[q * rp];
                     dst[q * N1] = make_float4(sa ? a.y : a.x, sb ? b.y : b.x, sa ? a.w : a.z, sb ? b.w : b.z);
                 }
             }
@@ -1216,26 +1224,22 @@ __global__ void __launch_bounds__(BLOCK) k_pack_pairs(const float *__restrict__ 
         const int i = (int)(t % pitch);
         const long long r = t / pitch;
         const int jp = (int)(r % njp), k = (int)(r / njp);
-        float v[2][16];
+        float v[2][10];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * jp + h;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) v[h][c] = 0.0f;
+            for (int c = 0; c < 10; ++c) v[h][c] = 0.0f;
             if (j >= nj) continue;
             const float *m = met + ((long long)k * nj + j) * pitch + i;
 #pragma unroll
             for (int c = 0; c < 9; ++c) v[h][c] = m[c * fs];
             v[h][9] = m[MET_JINV * fs];
-            v[h][10] = m[MET_CSD2 * fs] * m[MET_J * fs];
-            v[h][11] = m[MET_J * fs];
-            v[h][12] = m[MET_NORM * fs];
-            v[h][13] = m[(MET_NORM + 1) * fs];
-            v[h][14] = m[(MET_NORM + 2) * fs];
         }
-        float4 *out = mp + 8 * t;
+        float4 *out = mp + (r * 5) * pitch + i;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) out[q] = make_float4(v[0][2 * q], v[1][2 * q], v[0][2 * q + 1], v[1][2 * q + 1]);
+        for (int q = 0; q < 5; ++q)
+            out[q * pitch] = make_float4(v[0][2 * q], v[1][2 * q], v[0][2 * q + 1], v[1][2 * q + 1]);
     }
 }
 

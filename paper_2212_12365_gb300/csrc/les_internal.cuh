@@ -254,10 +254,11 @@ struct FusedJet {
     // (h, 1/h, h^(2/3), 0) with h the derivative of coordinate a along axis a
     const float4 *h1[3];
     // general form: the static fields of the two points of each row pair
-    // (rows 2p, 2p+1) of a column, interleaved point by point in eight
-    // float4: (m0 m1) (m2 m3) (m4 m5) (m6 m7) (m8, J^-1) ((Cs Delta)^2 J, J)
-    // (n0 n1) (n2, 0), m = the metric cofactors, n = the row norms; record of
-    // (i, pair p, k) at ((k * njp + p) * pitch + i) * 8
+    // (rows 2p, 2p+1) of a column, interleaved point by point in five
+    // float4: (m0 m1) (m2 m3) (m4 m5) (m6 m7) (m8, J^-1), m = the metric
+    // cofactors; float4 number q of (i, pair p, k) at
+    // ((k * njp + p) * 5 + q) * pitch + i, so that consecutive columns are
+    // consecutive in memory for every q
     const float4 *mp;
     // jets with no periodic i or j axis: tensor maps of the three state
     // registers for the TMA staging of the next plane (null: plain loads)
@@ -284,7 +285,7 @@ void launch_fused(const JetDev<float> *jets, const FusedJet *fj, int njets, int 
                   int wait_limit, const JetDev<float> *j1, const FusedJet *f1, cudaStream_t st);
 
 // General FP32 form: the paired static records (see FusedJet::mp) from the
-// FP32 static fields; mp holds nk * ((nj + 1) / 2) * pitch * 8 float4.
+// FP32 static fields; mp holds nk * ((nj + 1) / 2) * 5 * pitch float4.
 void launch_pack_pairs(const float *met, long long fs, int pitch, int nj, int nk, float4 *mp, cudaStream_t st);
 // Separable form: 1-D spacings of a Cartesian-product grid from device
 // coordinates (FP64 derivative stencils of the metric computation).
