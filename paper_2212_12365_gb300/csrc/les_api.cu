@@ -32,7 +32,7 @@ struct JetHost {
     size_t bytes;                      // size of this jet's region
     // device pointers (typed as bytes; the element type follows the precision)
     char *met, *q[3], *prim, *grad, *hflux, *rhs;
-    double *jinv64, *inflow_r;
+    double *jinv64, *inflow_ut;
     float4 *h1[3];                     // FP32: 1-D spacings of a product grid (separable form)
     float4 *mp;                        // FP32 general form: paired static records (5 float4 / row pair)
     int nblk_pt, nblk_bc[3];
@@ -240,7 +240,7 @@ static void plan_jet(const les_grid_desc *g, int prec, JetHost &J)
     J.grad = (char *)o_grad;
     J.hflux = (char *)o_hf;
     J.rhs = (char *)o_rhs;
-    J.inflow_r = (double *)o_inr;
+    J.inflow_ut = (double *)o_inr;
     J.h1[0] = prec == LES_FP32 ? (float4 *)o_h1 : nullptr;
     J.h1[1] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)g->ni * 16) : nullptr;
     J.h1[2] = prec == LES_FP32 ? (float4 *)(o_h1 + (size_t)(g->ni + g->nj) * 16) : nullptr;
@@ -313,7 +313,7 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.grad = (real *)J.grad;
     D.hflux = (real *)J.hflux;
     D.rhs = (real *)J.rhs;
-    D.inflow_r = J.inflow_r;
+    D.inflow_ut = J.inflow_ut;
     D.oob = h->d_oob;
     const les_params &p = J.prm;
     D.gamma = p.gamma;
@@ -370,14 +370,16 @@ template <typename real> static int setup_jet(les_handle *h, JetHost &J, const l
             CK(cudaGetLastError());
         }
     }
-    // radius of the inflow-face points
-    std::vector<double> r((size_t)J.n[1] * J.n[2]);
+    // inflow profile u~(r) = [1 + tanh((0.5 - r)/(2 theta))]/2 of the
+    // inflow-face points, r = (y^2 + z^2)^1/2 (static: formed once here)
+    std::vector<double> ut((size_t)J.n[1] * J.n[2]);
     for (int k = 0; k < J.n[2]; ++k)
         for (int j = 0; j < J.n[1]; ++j) {
             size_t p = ((size_t)k * J.n[1] + j) * J.n[0];
-            r[(size_t)k * J.n[1] + j] = std::sqrt(g->y[p] * g->y[p] + g->z[p] * g->z[p]);
+            const double r = std::sqrt(g->y[p] * g->y[p] + g->z[p] * g->z[p]);
+            ut[(size_t)k * J.n[1] + j] = 0.5 * (1.0 + std::tanh((0.5 - r) / (2.0 * J.prm.theta)));
         }
-    CK(cudaMemcpyAsync(J.inflow_r, r.data(), r.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(J.inflow_ut, ut.data(), ut.size() * 8, cudaMemcpyHostToDevice, h->st));
     // positive cell volumes
     std::vector<double> jv((size_t)J.fs);
     CK(cudaMemcpyAsync(jv.data(), J.jinv64, (size_t)J.fs * 8, cudaMemcpyDeviceToHost, h->st));
@@ -611,7 +613,7 @@ static int create_impl(const les_grid_desc *g, const les_params *p, int njets, v
         J.grad = jb + (size_t)J.grad;
         J.hflux = jb + (size_t)J.hflux;
         J.rhs = jb + (size_t)J.rhs;
-        J.inflow_r = (double *)(jb + (size_t)J.inflow_r);
+        J.inflow_ut = (double *)(jb + (size_t)J.inflow_ut);
         for (int a = 0; a < 3; ++a)
             if (J.h1[a]) J.h1[a] = (float4 *)(jb + (size_t)J.h1[a]);
         if (J.mp) J.mp = (float4 *)(jb + (size_t)J.mp);

@@ -76,7 +76,7 @@ struct JetDev {
     real *grad;        // NGRAD fields (scratch)
     real *hflux;       // NHF fields (scratch): interface fluxes
     real *rhs;         // NF fields (residual for diagnostics / debug)
-    const double *inflow_r; // nj*nk: radius sqrt(y^2+z^2) of the i = 0 face points
+    const double *inflow_ut; // nj*nk: inflow profile u~(r) of the i = 0 face points (host tanh)
     // flow parameters (jet units)
     double gamma, Pr, Pr_sgs, Re, mach, TR, theta, noise_amp, k2, k4, suth_S;
     double inv_Re;     // 1/Re (0 for an inviscid run)

@@ -349,6 +349,107 @@ template <typename T> __device__ void bc_exit(const BcK<T> &k, const T Qe[5], co
     Qf[4] = rho * (ei + T(0.5) * (e.u[0] * e.u[0] + e.u[1] * e.u[1] + e.u[2] * e.u[2]));
 }
 
+// FP32 storage: the boundary arithmetic runs in FP32 except the interior
+// pressure and the temperature difference T_e - T_inf = c_e^2 - c_inf^2,
+// which are formed in FP64 from the stored values.  The far-field face state
+// differs from the interior (or ambient) one by small amounts: the normal
+// velocity by (c_e - c_inf)/(gamma - 1) - q_n,e/2, the density and pressure by
+// factors (c_f/c)^m close to 1.  Each of these is computed as a difference
+// that is accurate relative to itself (c_e - c_inf from T_e - T_inf; the
+// factors as 1 + expm1(m log1p(x)) with x = c_f/c - 1 formed from small
+// terms), so that FP32 rounding does not seed pressure or transverse
+// momentum noise on the faces.
+struct BcF {
+    float g, g1, rg, TR, cinf, e2, e2g; // gamma, 1/(gamma-1), 1/gamma, ambient rho and c,
+                                        // 2/(gamma-1), 2 gamma/(gamma-1)
+    double gd, gm1d, Tinfd;             // gamma, gamma - 1, ambient T = c_inf^2 = 1/TR
+};
+
+__device__ __forceinline__ void cons_f(float rho, const float u[3], float p, const BcF &k, float Q[5])
+{
+    Q[0] = rho;
+    Q[1] = rho * u[0];
+    Q[2] = rho * u[1];
+    Q[3] = rho * u[2];
+    Q[4] = p * k.g1 + 0.5f * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+// Far field (Sec. "Far Field Boundary") for FP32 storage.  With
+// R+- = q_n +- 2c/(gamma-1) (R- of the ambient at rest, R+ of the interior):
+// q_n,f = (R+ + R-)/2 = q_n,e/2 + (c_e - c_inf)/(gamma-1) and
+// c_f = (gamma-1)(R+ - R-)/4 = (gamma-1) q_n,e/4 + (c_e + c_inf)/2.  The
+// isentropic density rho_e^gamma c_f^2 / (gamma p_e), raised to 1/(gamma-1),
+// is rho_e (c_f/c_e)^(2/(gamma-1)) since gamma p_e = rho_e c_e^2, and the face
+// pressure rho_f c_f^2 / gamma is p_e (c_f/c_e)^(2 gamma/(gamma-1)); on inflow
+// the same with the ambient state (rho_inf c_inf^2 = gamma p_inf = 1).
+__device__ void bc_farfield_f32(const BcF &k, const float Qe[5], const float n[3], float Qf[5])
+{
+    const double rho64 = Qe[0];
+    const double rr64 = 1.0 / rho64;
+    const double ke2 = ((double)Qe[1] * Qe[1] + (double)Qe[2] * Qe[2] + (double)Qe[3] * Qe[3]) * rr64; // rho |u|^2
+    const double p64 = k.gm1d * ((double)Qe[4] - 0.5 * ke2);
+    const double T64 = k.gd * p64 * rr64;
+    const float dT = (float)(T64 - k.Tinfd); // T_e - T_inf
+    const float rr = (float)rr64;
+    const float u[3] = {Qe[1] * rr, Qe[2] * rr, Qe[3] * rr};
+    const float ce = sqrtf((float)T64);
+    const float dc = dT / (ce + k.cinf); // c_e - c_inf
+    const float qne = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    const float mn = qne / ce;
+    if (mn >= 1.0f) { // supersonic outflow: all from inside
+        for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
+        return;
+    }
+    if (mn <= -1.0f) { // supersonic inflow: the ambient at rest
+        const float z[3] = {0.0f, 0.0f, 0.0f};
+        cons_f(k.TR, z, k.rg, k, Qf);
+        return;
+    }
+    const float qv = 0.25f * (k.g - 1.0f) * qne; // c_f = qv + (c_e + c_inf)/2
+    float uf[3], rho, p;
+    // subsonic outflow, and |M_n| <= 1e-8 (as in the FP64 form): entropy and
+    // tangential velocity from inside
+    if (mn >= -1e-8f) {
+        const float dq = k.g1 * dc - 0.5f * qne; // q_n,f - q_n,e
+        for (int c = 0; c < 3; ++c) uf[c] = u[c] + dq * n[c];
+        const float L = log1pf((qv - 0.5f * dc) / ce); // log(c_f/c_e)
+        const float rho_e = Qe[0], p_e = (float)p64;
+        rho = fmaf(rho_e, expm1f(k.e2 * L), rho_e);
+        p = fmaf(p_e, expm1f(k.e2g * L), p_e);
+    } else { // subsonic inflow: from the ambient (q_n,inf = 0)
+        const float qnf = 0.5f * qne + k.g1 * dc;
+        for (int c = 0; c < 3; ++c) uf[c] = qnf * n[c];
+        const float L = log1pf((qv + 0.5f * dc) / k.cinf); // log(c_f/c_inf)
+        rho = fmaf(k.TR, expm1f(k.e2 * L), k.TR);
+        p = fmaf(k.rg, expm1f(k.e2g * L), k.rg);
+    }
+    cons_f(rho, uf, p, k, Qf);
+}
+
+// Exit (Sec. "Exit Boundary Condition") for FP32 storage (the interior
+// pressure, e - rho |u|^2 / 2, in FP64).
+__device__ void bc_exit_f32(const BcF &k, const float Qe[5], const float n[3], float Qf[5])
+{
+    const double rr64 = 1.0 / (double)Qe[0];
+    const float rr = (float)rr64;
+    const float u[3] = {Qe[1] * rr, Qe[2] * rr, Qe[3] * rr};
+    const float q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float p = (float)(k.gm1d * ((double)Qe[4] -
+                                      0.5 * ((double)Qe[1] * Qe[1] + (double)Qe[2] * Qe[2] + (double)Qe[3] * Qe[3]) * rr64));
+    if ((u[0] * n[0] + u[1] * n[1] + u[2] * n[2]) * rsqrtf(k.g * p * rr) >= 1.0f) {
+        for (int t = 0; t < 5; ++t) Qf[t] = Qe[t];
+        return;
+    }
+    // p_f = p_inf = 1/gamma with the interior internal energy p/((gamma-1) rho)
+    const float ei = p * k.g1 * rr;
+    const float rho = Qe[0] / (k.g * p);
+    Qf[0] = rho;
+    Qf[1] = rho * u[0];
+    Qf[2] = rho * u[1];
+    Qf[3] = rho * u[2];
+    Qf[4] = rho * (ei + 0.5f * q2);
+}
+
 // Centerline (Sec. "Centerline Boundary Condition"): one thread per (axial
 // station i, conserved variable f) of a jet whose j- face is the axis sums the
 // unscaled ring j = 1 over k in index order (deterministic, the same sum for
@@ -383,6 +484,20 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
     return z ^ (z >> 31);
 }
 
+// Inflow noise of velocity component c at face point (jj, kk) for the step
+// that `level` counts (level > 0): A U_j (2h - 1), h in [0, 1) the top 53 bits
+// of SplitMix64 output number ((level - 1) nk + kk) nj + jj) * 3 + c.
+template <typename real>
+__device__ __forceinline__ double inflow_noise(const JetDev<real> &J, long long level, int kk, int jj, int c)
+{
+    const unsigned long long ctr =
+        ((((unsigned long long)(level - 1) * (unsigned long long)J.n[2] + (unsigned long long)kk) *
+              (unsigned long long)J.n[1] +
+          (unsigned long long)jj) * 3ull) + (unsigned long long)c;
+    const double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
+    return J.noise_amp * J.mach * (2.0 * h - 1.0);
+}
+
 template <typename real>
 __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ jets, BlockMap bm,
                                               int axis, int dst, const long long *__restrict__ level_p)
@@ -411,6 +526,60 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         const long long E = lidx(J, qe[0], qe[1], qe[2]);
         const long long fs = J.fs;
         real *Qd = J.q[dst];
+        const int jj = qf[1], kk = qf[2];
+        if constexpr (sizeof(real) == sizeof(float)) {
+            // FP32 storage: FP32 arithmetic (see bc_farfield_f32)
+            const BcF k{(float)J.gamma, (float)J.bc_g1, (float)J.bc_rg, (float)J.TR, (float)J.bc_cinf,
+                        (float)(2.0 * J.bc_g1), (float)(2.0 * J.gamma * J.bc_g1), J.gamma, J.gamma - 1.0, 1.0 / J.TR};
+            float n[3], nn = 0.0f;
+            const float sg = side ? 1.0f : -1.0f;
+            for (int c = 0; c < 3; ++c) {
+                n[c] = sg * (float)J.met[(3 * axis + c) * fs + F];
+                nn += n[c] * n[c];
+            }
+            const float rn = rsqrtf(nn);
+            for (int c = 0; c < 3; ++c) n[c] *= rn;
+            float Qe[5], Qf[5];
+            for (int f = 0; f < 5; ++f) Qe[f] = (float)Qd[f * fs + E];
+            if (type == LES_BC_FARFIELD) {
+                bc_farfield_f32(k, Qe, n, Qf);
+            } else if (type == LES_BC_EXIT) {
+                bc_exit_f32(k, Qe, n, Qf);
+            } else if (type == LES_BC_INFLOW_JET) {
+                const double utd = J.inflow_ut[(long long)kk * J.n[1] + jj];
+                if (utd < 0.01) {
+                    bc_farfield_f32(k, Qe, n, Qf);
+                } else {
+                    const float ut = (float)utd, M = (float)J.mach, g = k.g;
+                    float uf[3];
+                    float p, rho;
+                    if (M < 1.0f) {
+                        // subsonic entrance (see the FP64 form below)
+                        uf[0] = M * ut;
+                        if (level > 0) uf[0] += (float)inflow_noise(J, level, kk, jj, 0);
+                        const float rre = 1.0f / Qe[0];
+                        uf[1] = Qe[2] * rre;
+                        uf[2] = Qe[3] * rre;
+                        const float Ttot = 1.0f + 0.5f * (g - 1.0f) * M * M;
+                        const float Ts = Ttot / (1.0f + 0.5f * (g - 1.0f) * (uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2]));
+                        p = powf(Ts, g * k.g1) * k.rg;
+                        rho = g * p / Ts;
+                    } else {
+                        const float Tt = (1.0f / k.TR) * (1.0f - ut) + ut + 0.5f * (g - 1.0f) * M * M * ut * (1.0f - ut);
+                        p = k.rg;
+                        rho = 1.0f / Tt; // gamma p / T
+                        uf[0] = M * ut;
+                        uf[1] = uf[2] = 0.0f;
+                        if (level > 0)
+                            for (int c = 0; c < 3; ++c) uf[c] += (float)inflow_noise(J, level, kk, jj, c);
+                    }
+                    cons_f(rho, uf, p, k, Qf);
+                }
+            } else {
+                continue;
+            }
+            for (int f = 0; f < 5; ++f) Qd[f * fs + F] = (real)Qf[f];
+        } else {
         using T = double; // boundary arithmetic in FP64 (transcendental pow in the state precision)
         const BcK<T> k{(T)J.gamma, (T)J.bc_g1, (T)J.bc_rg, (T)J.TR, (T)J.bc_cinf};
         const T g = k.g;
@@ -432,9 +601,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         } else if (type == LES_BC_EXIT) {
             bc_exit<T>(k, Qe, n, Qf);
         } else if (type == LES_BC_INFLOW_JET) {
-            const int jj = qf[1], kk = qf[2];
-            const T rr = (T)J.inflow_r[(long long)kk * J.n[1] + jj];
-            const T ut = T(0.5) * (T(1) + tanh((T(0.5) - rr) / (T(2) * (T)J.theta)));
+            const T ut = (T)J.inflow_ut[(long long)kk * J.n[1] + jj];
             const T M = (T)J.mach;
             if (ut < T(0.01)) {
                 bc_farfield<T, real>(k, Qe, n, Qf);
@@ -444,14 +611,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
                 // point, T from the jet's total temperature 1 + (gamma-1) M^2/2
                 // with the face velocity in units of a_j, p = T^(gamma/(gamma-1))/gamma
                 T u = M * ut;
-                if (level > 0) {
-                    const unsigned long long ctr =
-                        (((unsigned long long)(level - 1) * (unsigned long long)J.n[2] + (unsigned long long)kk) *
-                             (unsigned long long)J.n[1] +
-                         (unsigned long long)jj) * 3ull;
-                    const double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
-                    u += (T)(J.noise_amp * J.mach * (2.0 * h - 1.0));
-                }
+                if (level > 0) u += (T)inflow_noise(J, level, kk, jj, 0);
                 const T rre = T(1) / Qe[0];
                 const T v = Qe[2] * rre, w = Qe[3] * rre;
                 const T Ttot = T(1) + T(0.5) * (g - T(1)) * M * M;
@@ -470,22 +630,15 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
                 s.rho = g * s.p / Tt;
                 s.u[0] = M * ut;
                 s.u[1] = s.u[2] = T(0);
-                if (level > 0) {
-                    for (int c = 0; c < 3; ++c) {
-                        unsigned long long ctr =
-                            ((((unsigned long long)(level - 1) * (unsigned long long)J.n[2] +
-                               (unsigned long long)kk) * (unsigned long long)J.n[1] +
-                              (unsigned long long)jj) * 3ull) + (unsigned long long)c;
-                        double h = (double)(splitmix64(J.seed, ctr) >> 11) * (1.0 / 9007199254740992.0);
-                        s.u[c] += (T)(J.noise_amp * J.mach * (2.0 * h - 1.0));
-                    }
-                }
+                if (level > 0)
+                    for (int c = 0; c < 3; ++c) s.u[c] += (T)inflow_noise(J, level, kk, jj, c);
                 cons_t(s, k, Qf);
             }
         } else {
             continue;
         }
         for (int f = 0; f < 5; ++f) Qd[f * fs + F] = (real)(jinvF * Qf[f]);
+        }
     }
 }
 
