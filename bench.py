@@ -30,10 +30,16 @@ sys.path.insert(0, ROOT)
 
 from paper_2212_12365_gb300 import inputs as I  # noqa: E402
 
-# Algorithmic FP64/FP32 operations per grid point and stage, counted from the
-# method (each interface flux once; FMA = 2, divide/sqrt = 1): primitives 96,
-# gradients and closures 141, three interface fluxes 765, update 41.
-FLOPS_PER_PT_STAGE = {"point": 96, "grads": 141, "iface": 765, "update": 41}
+# Algorithmic floating-point operations per grid point and stage, counted
+# from the method in the partition of the FP64 stage kernels (each point
+# quantity and each interface flux once; add/sub/mul = 1, FMA = 2,
+# divide/sqrt = 1, min/max/abs = 0): point pass 94 (the 5 multiplications of
+# the J^-1 Q scaling included; primitives, Sutherland, spectral radii and
+# lambda-bar, half point fluxes), gradients and closures 112, three interface
+# fluxes 3 x 158 = 474, update 35.  The FP32 fused stage does the same work
+# less the scaling and plus one J multiplication in the update: 711.
+FLOPS_PER_PT_STAGE = {"point": 94, "grads": 112, "iface": 474, "update": 35}
+FLOPS_PER_PT_STAGE_FUSED = 711
 # Algorithmic HBM bytes per point and stage: stages 2-5 read Q(l-1), Q(0) and 10
 # metric values and write Q(l); stage 1 reads Q(0) once: 24 values on average.
 ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
@@ -47,7 +53,10 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
 # describes the kernel that runs and the lookup gives None.
 _PAPER_JET = "jet-384x256x144"
 KERNEL_SOURCE = {"k_iface": "les_stage.cu", "k_fused": "les_fused.cu"}
-TRAFFIC_BYTES_PER_POINT = {}  # (workload, precision, kernel, decomposition) -> (bytes per point, source sha16)
+TRAFFIC_BYTES_PER_POINT = {  # (workload, precision, kernel, decomposition) -> (bytes per point, source sha16)
+    # profiles/stage_kernels_fp64_jet-384x256x144.md: 13431.0 + 1682.2 MB per launch
+    (_PAPER_JET, "fp64", "k_iface", None): (1067.64, "fb880ab93d8e0603"),
+}
 
 
 def source_sha16(kname: str):
@@ -82,7 +91,11 @@ def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str,
 # Arithmetic-pipe utilisation of the dominant kernel from the committed ncu
 # captures (sm__inst_executed_pipe_*, % of peak sustained while active), with
 # the source hash of the captured kernel as above
-PIPE_UTIL_NCU = {}  # (precision, kernel) -> (metrics dict, source sha16)
+PIPE_UTIL_NCU = {  # (precision, kernel) -> (metrics dict, source sha16)
+    # profiles/stage_kernels_fp64_jet-384x256x144.md (192x128x72 capture)
+    ("fp64", "k_iface"): ({"fp64_pipe_pct": 87.90, "executed_fp64_flop_per_point": 469.7,
+                          "dadd_dmul_dfma_per_point": [132.8, 85.2, 125.9]}, "fb880ab93d8e0603"),
+}
 # Nominal multiply-add throughput of GB300 (unit counts x the maximum clock),
 # reported beside the measured figures: 2 DFMA and 128 FFMA per clock and SM.
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -511,7 +524,7 @@ def run_ours(args):
         peak_source = "measured: DFMA loop of les_measure_peak on this GPU (CUDA events)"
     else:
         dom = "iface"  # the fused single-pass stage kernel is traced under this kind
-        kname, flops_pt = "k_fused", sum(FLOPS_PER_PT_STAGE.values())
+        kname, flops_pt = "k_fused", FLOPS_PER_PT_STAGE_FUSED
         peak, peak_nominal = alu["fp32_fma"], FP32_NOMINAL_TFLOPS
         peak_source = "measured: FFMA loop of les_measure_peak on this GPU (CUDA events)"
     t_launch = prof[dom][0] / max(prof[dom][1], 1) / 1e3  # s per launch

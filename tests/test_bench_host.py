@@ -58,3 +58,11 @@ def test_hbm_denominator_is_labelled(monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: {})
     v, src = bench.hbm_peak_gbs()
     assert v == 6800.0 and src.startswith("fallback")
+
+
+def test_flop_counts_of_the_two_forms():
+    # the FP32 fused stage: the FP64 kernels' work less the 5 multiplications
+    # of the J^-1 Q scaling, plus one J multiplication in the update
+    assert sum(bench.FLOPS_PER_PT_STAGE.values()) == 715
+    assert bench.FLOPS_PER_PT_STAGE_FUSED == 715 - 5 + 1
+    assert bench.FLOPS_PER_PT_STAGE["iface"] == 3 * 158
