@@ -125,7 +125,8 @@ template <int TY, bool SEP> struct Geo {
     static constexpr unsigned BOX_BYTES = 4u * 5 * BR * TMA_BOX_X;
     static_assert(BOX_BYTES % 16 == 0, "box size");
     static constexpr size_t O_MBAR = O_QG + BOX_BYTES;
-    static constexpr size_t BYTES = O_MBAR + 8;
+    static constexpr size_t O_FPS = O_MBAR + 8;
+    static constexpr size_t BYTES = O_FPS + 64;
     static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
 
@@ -137,6 +138,7 @@ template <int TY, bool SEP> struct Sm {
     float4 *HX, *HY, *HZ;
     float *QG;
     unsigned long long *MBAR;
+    float *FPS; // a batch jet's constants (FusedParams) for the item
     __device__ __forceinline__ explicit Sm(unsigned char *b)
         : PA((float4 *)(b + Geo<TY, SEP>::O_PA)), PB((float4 *)(b + Geo<TY, SEP>::O_PB)),
           PC((float4 *)(b + Geo<TY, SEP>::O_PC)), PH((float2 *)(b + Geo<TY, SEP>::O_PH)),
@@ -145,7 +147,8 @@ template <int TY, bool SEP> struct Sm {
           QZ((float *)(b + Geo<TY, SEP>::O_QZ)),
           HX((float4 *)(b + Geo<TY, SEP>::O_HX)), HY((float4 *)(b + Geo<TY, SEP>::O_HY)),
           HZ((float4 *)(b + Geo<TY, SEP>::O_HZ)),
-          QG((float *)(b + Geo<TY, SEP>::O_QG)), MBAR((unsigned long long *)(b + Geo<TY, SEP>::O_MBAR))
+          QG((float *)(b + Geo<TY, SEP>::O_QG)), MBAR((unsigned long long *)(b + Geo<TY, SEP>::O_MBAR)),
+          FPS((float *)(b + Geo<TY, SEP>::O_FPS))
     {
     }
 };
@@ -434,6 +437,16 @@ template <bool ONE, typename T> __device__ __forceinline__ const T &jet_entry(co
     else return tab[j];
 }
 
+// The jet's constants: the kernel parameter (ONE), else the item's copy in
+// shared memory (read with broadcast loads instead of global loads).
+template <bool ONE>
+__device__ __forceinline__ const FusedParams &jet_params(const FusedParams &param, const float *staged)
+{
+    if constexpr (ONE) return param;
+    else return *reinterpret_cast<const FusedParams *>(staged);
+}
+static_assert(sizeof(FusedParams) % 4 == 0 && sizeof(FusedParams) <= 64, "FusedParams staging");
+
 template <int TY, bool SEP, bool ONE>
 __global__ void __launch_bounds__(FX * TY / 2, 1)
     k_fused(const JetDev<float> *__restrict__ jets, const FusedJet *__restrict__ fj, int njets,
@@ -523,7 +536,13 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         }
         const JetDev<float> &J = jet_entry<ONE>(j1, jets, jet);
         const FusedJet &F = jet_entry<ONE>(f1, fj, jet);
-        const FusedParams &FP = F.fp;
+        if constexpr (!ONE) {
+            // staged for the item (the previous item's last reads of FPS
+            // precede its closing barrier; the item barrier below publishes it)
+            constexpr int NFP = sizeof(FusedParams) / 4;
+            if (tid >= NT - NFP) S.FPS[tid - (NT - NFP)] = reinterpret_cast<const float *>(&F.fp)[tid - (NT - NFP)];
+        }
+        const FusedParams &FP = jet_params<ONE>(F.fp, S.FPS);
         const int ni = J.n[0], nj = J.n[1], nk = J.n[2];
         const int pi = J.per[0], pj = J.per[1], pk = J.per[2];
         // output ranges; on a periodic j axis the tiles start at row 1 (so that
