@@ -276,18 +276,10 @@ template <typename T> __device__ __forceinline__ PrimT<T> prim_t(const T Q[5], T
     return s;
 }
 
-// x^y in the precision P of the stored state: the isentropic density update
-// of the far-field condition is the only transcendental of the boundary pass,
-// and FP64 pow is slow on this GPU; the Riemann-invariant arithmetic, where
-// q_n,f ~ c_e - c_inf cancels, stays in FP64.
-template <typename P> __device__ __forceinline__ double bc_pow(double x, double y)
-{
-    return (double)pow((P)x, (P)y);
-}
 
 // Far field (Sec. "Far Field Boundary"): Riemann invariants along the unit
 // outward normal n; R- from the ambient at rest, R+ from the interior point.
-template <typename T, typename P = T>
+template <typename T>
 __device__ void bc_farfield(const BcK<T> &k, const T Qe[5], const T n[3], T Qf[5])
 {
     const T g = k.g;
@@ -320,10 +312,10 @@ __device__ void bc_farfield(const BcK<T> &k, const T Qe[5], const T n[3], T Qf[5
     if (mn >= T(-1e-8)) {
         // rho_f = (rho_e^gamma c_f^2 / (gamma p_e))^(1/(gamma-1)), gamma p_e = rho_e c_e^2
         for (int c = 0; c < 3; ++c) f.u[c] = e.u[c] + (qnf - qne) * n[c];
-        f.rho = bc_pow<P>(bc_pow<P>(e.rho, g) * cf * cf * (rr * rce * rce), k.g1);
+        f.rho = pow(pow(e.rho, g) * cf * cf * (rr * rce * rce), k.g1);
     } else { // subsonic inflow: from the ambient (q_n,inf = 0, gamma p_inf = 1)
         for (int c = 0; c < 3; ++c) f.u[c] = T(0) + (qnf - T(0)) * n[c];
-        f.rho = bc_pow<P>(bc_pow<P>(rinf, g) * cf * cf, k.g1);
+        f.rho = pow(pow(rinf, g) * cf * cf, k.g1);
     }
     f.p = f.rho * cf * cf * k.rg;
     cons_t(f, k, Qf);
@@ -580,7 +572,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
             }
             for (int f = 0; f < 5; ++f) Qd[f * fs + F] = (real)Qf[f];
         } else {
-        using T = double; // boundary arithmetic in FP64 (transcendental pow in the state precision)
+        using T = double; // FP64 storage: boundary arithmetic in FP64
         const BcK<T> k{(T)J.gamma, (T)J.bc_g1, (T)J.bc_rg, (T)J.TR, (T)J.bc_cinf};
         const T g = k.g;
         // unit outward normal from the face point's metric row
@@ -597,14 +589,14 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
         T Qe[5], Qf[5];
         for (int f = 0; f < 5; ++f) Qe[f] = Qd[f * fs + E] * rjE;
         if (type == LES_BC_FARFIELD) {
-            bc_farfield<T, real>(k, Qe, n, Qf);
+            bc_farfield<T>(k, Qe, n, Qf);
         } else if (type == LES_BC_EXIT) {
             bc_exit<T>(k, Qe, n, Qf);
         } else if (type == LES_BC_INFLOW_JET) {
             const T ut = (T)J.inflow_ut[(long long)kk * J.n[1] + jj];
             const T M = (T)J.mach;
             if (ut < T(0.01)) {
-                bc_farfield<T, real>(k, Qe, n, Qf);
+                bc_farfield<T>(k, Qe, n, Qf);
             } else if (M < T(1)) {
                 // Sec. "Entrance Boundary", subsonic entrance: u fixed (profile
                 // and the u noise of the level), v and w from the interior
@@ -617,7 +609,7 @@ __global__ void __launch_bounds__(BLOCK) k_bc(const JetDev<real> *__restrict__ j
                 const T Ttot = T(1) + T(0.5) * (g - T(1)) * M * M;
                 const T Ts = Ttot / (T(1) + T(0.5) * (g - T(1)) * (u * u + v * v + w * w));
                 PrimT<T> s;
-                s.p = bc_pow<real>(Ts, g * k.g1) * k.rg;
+                s.p = pow(Ts, g * k.g1) * k.rg;
                 s.rho = g * s.p / Ts;
                 s.u[0] = u;
                 s.u[1] = v;

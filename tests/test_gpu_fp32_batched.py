@@ -104,16 +104,16 @@ def test_batched_bit_identical_to_single_fp64():
 
 def test_batched_fp32_against_oracle():
     """One jet of the batch, 20 steps from the ambient start, against the FP64
-    oracle: relative L2 <= 1e-5 for every field in the interior and for rho,
-    rho u and e over the whole grid.  The transverse momenta (only the inflow
-    noise and its start-up waves, ~1e-3 of rho u) may exceed it over the whole
-    grid by the far-field condition of the inflow plane: outside the jet the
-    entrained ambient flow crosses that plane with a normal velocity near
-    zero, where the paper's condition switches the tangential velocity and
-    entropy between the interior and the freestream (Sec. "Far Field
-    Boundary"), so FP32 rounding of the interior state can select the other
-    branch at a few face points.  That excess must sit on the inflow plane
-    (at least 90 % of the squared error) and stay below 1e-4."""
+    oracle: relative L2 <= 1e-5 for every field, over the whole grid and in
+    the interior.  The transverse momenta (only the inflow noise and its
+    start-up waves, ~1e-3 of rho u) are the sensitive fields: outside the jet
+    the entrained ambient flow crosses the inflow plane with a normal velocity
+    near zero, where the far-field condition switches the tangential velocity
+    and entropy between the interior and the freestream (Sec. "Far Field
+    Boundary"), so FP32 rounding of the face state could select the other
+    branch at a few face points; the FP32 boundary arithmetic forms its small
+    differences accurately (c_e - c_inf from T_e - T_inf in FP64), which keeps
+    this jet's faces on the FP64 branches."""
     jets = I.batch_jets(3, seed=12)
     specs = [g for g, _ in jets]
     fps = [f for _, f in jets]
@@ -132,9 +132,7 @@ def test_batched_fp32_against_oracle():
     whole, inner, share = error_split(got, ref, g.dims)
     print("batched fp32 jet 1, 20 steps, rel L2 per field:", whole, " interior:", inner, " i=0 share:", share)
     assert np.all(inner <= 1e-5), inner
-    assert np.all(whole[[0, 1, 4]] <= 1e-5), whole
-    for f in (2, 3):
-        assert whole[f] <= 1e-5 or (whole[f] <= 1e-4 and share[f] >= 0.9), (f, whole, share)
+    assert np.all(whole <= 1e-5), (whole, share)
 
 
 @pytest.mark.parametrize("prec", [les.LES_FP32, les.LES_FP32_SEPARABLE])
