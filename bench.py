@@ -57,10 +57,10 @@ TRAFFIC_BYTES_PER_POINT = {  # (workload, precision, kernel, decomposition) -> (
     # profiles/stage_kernels_fp64_jet-384x256x144.md: 13431.0 + 1682.2 MB per launch
     (_PAPER_JET, "fp64", "k_iface", None): (1067.64, "fb880ab93d8e0603"),
     # profiles/fused_stage_fp32_jet-384x256x144.md and ..._separable_...
-    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.39, "cf196a6accf2586f"),
-    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.49, "cf196a6accf2586f"),
-    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=balanced"): (77.25, "cf196a6accf2586f"),
-    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): (55.69, "cf196a6accf2586f"),
+    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.45, "37b78006e805df85"),
+    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.56, "37b78006e805df85"),
+    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=balanced"): (77.27, "37b78006e805df85"),
+    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): (55.68, "37b78006e805df85"),
 }
 
 
@@ -103,10 +103,10 @@ PIPE_UTIL_NCU = {  # (precision, kernel) -> (metrics dict, source sha16)
     # profiles/fused_stage_fp32_jet-384x256x144.md (192x128x72 capture, 32x16 tiles)
     ("fp32", "k_fused"): ({"fma_pipe_pct": 32.0, "fmaheavy_pct": 32.3, "fmalite_pct": 31.0, "issue_active_pct": 37.6,
                           "executed_fp32_flop_per_point": 1316.9, "thread_instructions_per_point": 1187.4},
-                         "cf196a6accf2586f"),
+                         "37b78006e805df85"),
     ("fp32-sep", "k_fused"): ({"fma_pipe_pct": 28.9, "fmaheavy_pct": 30.1, "fmalite_pct": 27.4,
                               "issue_active_pct": 38.3, "executed_fp32_flop_per_point": 782.4,
-                              "thread_instructions_per_point": 862.7}, "cf196a6accf2586f"),
+                              "thread_instructions_per_point": 862.7}, "37b78006e805df85"),
 }
 # Nominal multiply-add throughput of GB300 (unit counts x the maximum clock),
 # reported beside the measured figures: 2 DFMA and 128 FFMA per clock and SM.
