@@ -7,7 +7,8 @@ never imports, links or calls it, and it shares no code with the library.
 The arithmetic lives in ``les_oracle.c`` (plain C loops, FP64, written from
 the paper's sections in their order; see that file's header for the list of
 readings of garbled equations).  This module only builds it with gcc and
-marshals numpy arrays through ctypes.
+marshals numpy arrays through ctypes.  ``oracle.fwh`` (plain numpy, FP64) is
+the far-field FW-H integral of the probe surface's data.
 
 Parameter vector layout (``Params.as_array``):
   [gamma, Pr, Pr_sgs, Cs, k2, k4, Re, mach_j, TR, T_inf_dim, S1_dim, theta,
