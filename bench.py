@@ -421,6 +421,83 @@ def large_probe_form(args, les, torch):
     return out
 
 
+# FP32 operations per (panel, observer, time) evaluation of the FW-H observer
+# pass: emission-frame position 2, seven retarded interpolations 21, the two
+# radial projections 10, the integrand 5, the compensated sum 4.
+FWH_FLOP_PER_EVAL = 42
+
+
+def fwh_form(les, torch, alu):
+    """FW-H far-field pressure (les_fwh) on the large jet's probe surface
+    (r = 3D, 256 azimuths x 384 axial stations over x = 0.5..29.5): 1024
+    synthetic FP32 frames (four seeded monopoles on the jet axis radiating
+    Gaussian pulses into the ambient of temperature ratio 2, so the data are
+    an exact acoustic field), 64 microphones on an arc of radius 60D about
+    x = 15D from 20 to 120 degrees, 512 observer times.  Device time of the
+    observer pass per evaluation, its FP32 FLOP rate against the measured
+    FFMA peak, and the oracle's rate on a bounded sample (the CPU baseline;
+    parity is the tests' business)."""
+    from oracle import fwh as ofwh
+    TR = 2.0
+    c0, rho0, p0 = (1.0 / TR) ** 0.5, TR, 1.0 / 1.4
+    xyz, nrm, area = I.cylinder_panels(3.0, 256, 384, 0.5, 29.5)
+    obs = I.observer_arc(60.0, 64, 15.0)
+    nfr, dtau, nt, dt_obs = 1024, 0.1, 512, 0.1
+    rng = np.random.default_rng(2212)
+    src_x = rng.uniform(3.0, 25.0, 4)
+    t_c = rng.uniform(20.0, 60.0, 4)
+    amp = rng.uniform(0.05, 0.2, 4)
+    dev = torch.device("cuda")
+    P = torch.tensor(xyz, dtype=torch.float64, device=dev)
+    ring = torch.empty((nfr, 5, xyz.shape[1]), dtype=torch.float32, device=dev)
+    sig = 1.5
+    for m in range(nfr):
+        t = m * dtau
+        p = torch.zeros(xyz.shape[1], dtype=torch.float64, device=dev)
+        u = torch.zeros((3, xyz.shape[1]), dtype=torch.float64, device=dev)
+        for s_, (sx, tc, a) in enumerate(zip(src_x, t_c, amp)):
+            d = P.clone()
+            d[0] -= sx
+            R = torch.sqrt((d * d).sum(dim=0))
+            tr = t - R / c0
+            q = a * torch.exp(-((tr - tc) / sig) ** 2)
+            qd = -2.0 * (tr - tc) / sig ** 2 * q
+            p += rho0 * qd / (4 * np.pi * R)
+            u += (qd / (4 * np.pi * c0 * R) + q / (4 * np.pi * R * R)) * d / R
+        ring[m, 0] = (rho0 + p / c0 ** 2).float()
+        ring[m, 1:4] = u.float()
+        ring[m, 4] = (p0 + p).float()
+    d = obs[:, :, None] - xyz[:, None, :]
+    r = np.sqrt((d * d).sum(axis=0))
+    t0 = r.max() / c0 + 0.05
+    assert t0 + (nt - 1) * dt_obs - r.min() / c0 <= (nfr - 1) * dtau
+    torch.cuda.synchronize()
+    les.les_fwh(ring.data_ptr(), les.LES_FP32, nfr, nfr, xyz, nrm, area, dtau, p0, c0, obs, t0, dt_obs, nt)
+    t_wall = time.perf_counter()
+    out, ms = les.les_fwh(ring.data_ptr(), les.LES_FP32, nfr, nfr, xyz, nrm, area, dtau, p0, c0, obs, t0, dt_obs,
+                          nt, timings=True)
+    t_wall = time.perf_counter() - t_wall
+    evals = float(xyz.shape[1]) * obs.shape[1] * nt
+    tflops = evals * FWH_FLOP_PER_EVAL / (ms[1] * 1e-3) / 1e12
+    # CPU baseline: the oracle on a bounded sample of the same evaluation
+    # (every 16th panel, one microphone, 24 observer times)
+    sub = np.arange(0, xyz.shape[1], 16)
+    host = ring[:, :, sub].double().cpu().numpy()
+    t_cpu = time.perf_counter()
+    ofwh.pressure(host, xyz[:, sub], nrm[:, sub], area[sub], dtau, rho0, p0, c0, obs[:, 32:33], t0, dt_obs * 21, 24)
+    t_cpu = time.perf_counter() - t_cpu
+    return {"metric": "FW-H panel-observer-time evaluations/s", "value": evals / (ms[1] * 1e-3),
+            "panels": int(xyz.shape[1]), "frames": nfr, "observers": int(obs.shape[1]), "times": nt,
+            "ms_source_pass": float(ms[0]), "ms_observer_pass": float(ms[1]), "wall_s_call": t_wall,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": alu["fp32_fma"], "unit": "TFLOP/s",
+                         "frac": tflops / alu["fp32_fma"], "flop_per_eval": FWH_FLOP_PER_EVAL,
+                         "peak_source": "measured: FFMA loop of les_measure_peak on this GPU (CUDA events)"},
+            "cpu_baseline": {"value": len(sub) * 24 / t_cpu, "unit": "panel-observer-time evaluations/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sub)} panels (every 16th) x 1 microphone x 24 times, numpy"},
+            "p_rms_over_p0": float(np.sqrt((out ** 2).mean()) / p0)}
+
+
 def precision_form(args, spec, fp, les, torch, fp64_value):
     """FP32 storage/arithmetic on the same grid (metrics and sums in FP64): its
     rate, speedup over the FP64 path, and relative L2 per field against the FP64
@@ -596,7 +673,7 @@ def run_ours(args):
         if one:
             cpu["value_1core"] = one["value"]
             cpu["sample_1core"] = one["sample"] + ", 1 thread"
-    secondary = batched = large = None
+    secondary = batched = large = fwh_line = None
     default_run = rank == 0 and ws == 1 and args.workload == "jet-384x256x144" and prec == "fp64"
     if default_run and not args.no_fp32:
         secondary = precision_form(args, spec, fp, les, torch, value)
@@ -605,6 +682,7 @@ def run_ours(args):
         solver = None
         batched = batched_form(args, les, torch, value)
         large = large_probe_form(args, les, torch)
+        fwh_line = fwh_form(les, torch, alu)
 
     if rank == 0:
         line = {"metric": "grid-point-stage updates/s", "value": value,
@@ -622,6 +700,7 @@ def run_ours(args):
                 "precision_form": secondary,
                 "batched": batched,
                 "large_probe": large,
+                "fwh": fwh_line,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if solver is not None:

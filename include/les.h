@@ -324,6 +324,43 @@ int les_diag_sums_noalloc(const double *qhat, const double *rhs, int64_t npoints
 #define LES_PEAK_FP32X2_FMA 2
 int les_measure_peak(int kind, double *tflops);
 
+/* Far-field acoustic pressure from the probe surface's frames by the Ffowcs
+ * Williams-Hawkings equation (the paper names FW-H as the far-field step fed
+ * by its probe surface, Secs. "Introduction" and "Concluding Remarks", but
+ * gives no formulation).  Adopted: Farassat's Formulation 1A (NASA
+ * TM-2007-214853, 2007) with the permeable-surface source terms of
+ * di Francescantonio (J. Sound Vib. 202, 1997) for a surface at rest in a
+ * medium at rest (ambient pressure p0, sound speed c0):
+ *   Q = rho u.n, L_i = (p - p0) n_i + rho u_i u.n,
+ *   4 pi p'(x, t) = sum over panels of A [dQ/dtau / r + (dL_r/dtau)/(c0 r) + L_r/r^2]
+ * at the emission time tau = t - r/c0 (r = |x - y|, L_r = L.(x - y)/r);
+ * d/dtau by second-order differences between frames (central; one-sided at
+ * the first and last frame), values at tau by linear interpolation between
+ * frames.
+ * ring: device array [capacity][5][npts] of (rho, u, v, w, p), double for
+ *   precision LES_FP64, float for LES_FP32 / LES_FP32_SEPARABLE, as
+ *   les_probe_surface fills it; frames_written: frames written so far
+ *   (les_probe_frames).  The last min(frames_written, capacity) frames are
+ *   used in time order, the oldest of them at tau = 0, frame m at m dtau.
+ * xyz, nrm: host, 3*npts each (all x, then y, then z): panel centres (the
+ *   probe points, in the ring's point order) and unit outward normals;
+ *   area: host, npts panel areas.
+ * obs: host, 3*nobs observer positions; observer times t_k = t0 + k dt_obs,
+ *   k < nt, on the tau axis.  Every emission time t_k - r/c0 must lie within
+ *   [0, (frames - 1) dtau] for every panel and observer.
+ * p_out: host, nobs*nt doubles, layout [observer][time]: p' = p - p0.
+ * ms_out: NULL, or 2 doubles receiving the device time (ms) of the source
+ *   pass and of the observer pass.
+ * Allocates device scratch (32 bytes per panel and frame, plus partial sums)
+ * for the call and frees it; runs on `stream`, synchronises it.  The sums
+ * have a fixed order: the same inputs give the same bits.  Errors:
+ * LES_ERR_ARG (null pointer, fewer than 3 frames, an emission time outside
+ * the frames, an observer on a panel; text in les_last_error(NULL)),
+ * LES_ERR_OOM, LES_ERR_CUDA. */
+int les_fwh(const void *ring, int precision, int capacity, int64_t frames_written, int npts, const double *xyz,
+            const double *nrm, const double *area, double dtau, double p0, double c0, int nobs, const double *obs,
+            double t0, double dt_obs, int nt, double *p_out, void *stream, double *ms_out);
+
 /* Human-readable description of a handle: precision, jets, device bytes and
  * the stage kernel configuration chosen by the autotuner (FP32: fused tile
  * height and k-chunk; FP64: four-kernel stage).  Valid until the next call

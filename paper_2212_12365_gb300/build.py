@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libles.so")
-SOURCES = ["les_kernels.cu", "les_stage.cu", "les_fused.cu", "les_api.cu", "les_noalloc.cu", "les_peak.cu"]
+SOURCES = ["les_kernels.cu", "les_stage.cu", "les_fused.cu", "les_api.cu", "les_noalloc.cu", "les_peak.cu", "les_fwh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

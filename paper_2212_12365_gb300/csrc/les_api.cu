@@ -113,6 +113,10 @@ struct les_handle {
 // (returned by les_last_error(NULL)).
 static thread_local std::string g_create_err;
 
+namespace les {
+void set_call_error(const char *msg) { g_create_err = msg; }
+} // namespace les
+
 static int fail(les_handle *h, int code, const std::string &msg)
 {
     if (h) h->err = msg;

@@ -271,6 +271,9 @@ struct FusedJet {
 constexpr int TMA_BOX_X = 40;
 constexpr int tma_box_rows(int ty) { return ty + 4; }
 
+// Error text of the handle-free entry points (les_last_error(NULL)).
+void set_call_error(const char *msg);
+
 template <int TY> int fused_prepare();
 // resident CTAs per SM of the fused stage for tile height ty (general or
 // separable form), from the occupancy calculator; 1 if it cannot tell

@@ -276,6 +276,29 @@ def cylinder_points(r: float, n_theta: int, n_x: int, x0: float, x1: float) -> n
     return np.stack([X.reshape(-1), (r * np.cos(TH)).reshape(-1), (r * np.sin(TH)).reshape(-1)])
 
 
+def cylinder_panels(r: float, n_theta: int, n_x: int, x0: float, x1: float):
+    """The probe cylinder of cylinder_points as FW-H panels: centres (the same
+    points, same order), unit outward (radial) normals and areas
+    r dtheta dx, halved at the two axial ends (trapezoid weights; the end
+    caps are left open)."""
+    xyz = cylinder_points(r, n_theta, n_x, x0, x1)
+    th = np.arange(n_theta) * 2 * np.pi / n_theta
+    TH = np.broadcast_to(th[None, :], (n_x, n_theta)).reshape(-1)
+    nrm = np.stack([np.zeros_like(TH), np.cos(TH), np.sin(TH)])
+    wx = np.full(n_x, (x1 - x0) / (n_x - 1))
+    wx[0] *= 0.5
+    wx[-1] *= 0.5
+    area = np.repeat(wx * r * 2 * np.pi / n_theta, n_theta)
+    return xyz, nrm, area
+
+
+def observer_arc(radius: float, n: int, x_centre: float, deg0: float = 20.0, deg1: float = 120.0) -> np.ndarray:
+    """Far-field microphones on an arc in the x-y plane about (x_centre, 0, 0),
+    angles from the jet axis deg0..deg1: 3 x n."""
+    a = np.radians(np.linspace(deg0, deg1, n))
+    return np.stack([x_centre + radius * np.cos(a), radius * np.sin(a), np.zeros(n)])
+
+
 def polar_jet_grid(ni: int, nj: int, nk: int, Lx: float, R: float, spacing_ratio: float = 6.0,
                    width: float = 0.5, spreading: float = 0.094, x_developed: float = 20.0) -> GridSpec:
     """The paper's jet mesh (Sec. "Mesh Generation"): a 2-D (x, r) mesh

@@ -35,7 +35,7 @@ EXPORTED = [
     "les_get_time", "les_probe_surface", "les_probe_frames", "les_get_diagnostics",
     "les_get_diagnostics_jet", "les_debug_rhs", "les_debug_field", "les_profile_step",
     "les_set_fused_tiling", "les_debug_stage_wait", "les_last_launch_count", "les_bounds_checking", "les_bounds_violation",
-    "les_diag_sums_noalloc", "les_measure_peak", "les_describe",
+    "les_diag_sums_noalloc", "les_measure_peak", "les_fwh", "les_describe",
     "les_last_error", "les_destroy",
 ]
 
@@ -104,6 +104,9 @@ def lib():
         L.les_bounds_violation.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.les_diag_sums_noalloc.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.les_measure_peak.argtypes = [ctypes.c_int, _dp]
+        L.les_fwh.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, vp, _dp]
         L.les_describe.argtypes = [vp]
         L.les_describe.restype = ctypes.c_char_p
         L.les_last_error.argtypes = [vp]
@@ -328,6 +331,28 @@ def les_measure_peak(kind: int) -> float:
     v = ctypes.c_double(0.0)
     _check(None, lib().les_measure_peak(int(kind), ctypes.byref(v)))
     return float(v.value)
+
+
+def les_fwh(ring_ptr: int, precision: int, capacity: int, frames_written: int, xyz, nrm, area, dtau: float,
+            p0: float, c0: float, obs, t0: float, dt_obs: float, nt: int, stream=None, timings: bool = False):
+    """Far-field pressure p' [nobs][nt] by the FW-H integral over the probe
+    surface's frames (see include/les.h); with timings=True also the device
+    times (ms) of the source and observer passes."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    nrm = np.ascontiguousarray(nrm, dtype=np.float64)
+    area = np.ascontiguousarray(area, dtype=np.float64)
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    npts = area.shape[0]
+    nobs = obs.shape[1]
+    assert xyz.shape == (3, npts) and nrm.shape == (3, npts) and obs.shape == (3, nobs)
+    out = np.empty((nobs, nt), dtype=np.float64)
+    ms = np.zeros(2, dtype=np.float64)
+    st = stream if stream is not None else current_stream()
+    _check(None, lib().les_fwh(ctypes.c_void_p(ring_ptr), int(precision), int(capacity), int(frames_written),
+                               int(npts), _dptr(xyz), _dptr(nrm), _dptr(area), float(dtau), float(p0), float(c0),
+                               int(nobs), _dptr(obs), float(t0), float(dt_obs), int(nt), _dptr(out), st,
+                               _dptr(ms) if timings else None))
+    return (out, ms) if timings else out
 
 
 def les_destroy(h):
