@@ -769,11 +769,19 @@ def main():
                          "instead of autotuning")
     ap.add_argument("--sweep", action="store_true",
                     help="throughput over the paper's ten mesh sizes (polar meshes), FP64 and FP32")
+    ap.add_argument("--fwh", action="store_true",
+                    help="only the FW-H far-field evaluation of the default run's 'fwh' key (one JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.sweep:
         run_sweep(args)
+    elif args.fwh:
+        import torch
+        from paper_2212_12365_gb300 import build, les
+        build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(fwh_form(les, torch, alu_peaks(les))), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
