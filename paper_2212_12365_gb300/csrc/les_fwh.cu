@@ -12,17 +12,18 @@
 // (one-sided three-point at the first and last frame), retarded values by
 // linear interpolation between the two frames around tau.
 //
-// Three kernels.  k_fwh_src forms, per panel and frame, L and the derivatives
+// Kernels.  k_fwh_src forms, per panel and frame, L and the derivatives
 // dQ/dtau, dL/dtau in FP64 from the ring (either precision) and stores them as
-// two float4 per (panel, frame), panel-major, so that the threads of a warp,
-// which handle consecutive observer times, read consecutive frames of one
-// panel.  k_fwh_obs: a CTA per (block of 256 observer times, observer, panel
-// chunk); for each sub-chunk of 256 panels the CTA first forms the panel's
-// distance, direction and weight for its observer in shared memory, then
-// every thread adds the panels' contributions to its observer time
-// (compensated FP32 within a sub-chunk, FP64 across sub-chunks) and writes
-// its chunk's partial sum; k_fwh_sum adds the chunks in chunk order.  Every
-// sum has a fixed order, so the result is the same on every run.
+// two float4 per (panel, frame), panel-major.  The observer pass, in one of
+// two forms: k_fwh_obs_win (staged) takes a block of 256 observer times, a
+// group of up to 16 microphones and a panel chunk per CTA, stages each
+// panel's window of source frames in shared memory once and evaluates every
+// microphone against it; k_fwh_obs (direct, when a window would not fit)
+// takes one microphone per CTA and reads the frames from global memory.  In
+// both, each thread is one observer time and sums its panels' contributions
+// (compensated FP32 within a stage of panels, FP64 across stages), and each
+// CTA writes its chunk's partial sums; k_fwh_sum adds the chunks in chunk
+// order.  Every sum has a fixed order, so the result is the same on every run.
 #include <cmath>
 #include <string>
 #include <vector>
@@ -171,6 +172,98 @@ __global__ void __launch_bounds__(FWH_T) k_fwh_obs(const float4 *__restrict__ sr
     if (k < nt) part[((long long)c * nobs + o) * nt + k] = acc;
 }
 
+// Observer pass with shared-memory reuse: a CTA per (256 observer times,
+// group of up to MG microphones, panel chunk).  Per group of G panels the CTA
+// forms every (panel, microphone) geometry, stages each panel's window of W
+// consecutive source frames (all the emission frames any of its microphones
+// needs for the block's 256 times) from global into shared memory once, and
+// then every thread (one observer time) evaluates all microphones against the
+// staged windows, with a compensated FP32 sum over the group's panels added
+// to its FP64 accumulator per microphone (in shared memory).  Each source
+// frame is read from global memory once per CTA instead of once per
+// (microphone, time) evaluation.
+__global__ void __launch_bounds__(FWH_T) k_fwh_obs_win(const float4 *__restrict__ src, int npts, int N,
+                                                       const double *__restrict__ xyz, const double *__restrict__ area,
+                                                       const double *__restrict__ obs, int nobs, int MG, double t0,
+                                                       double dt_obs, int nt, double dtau, double c0, int chunk, int G,
+                                                       int W, double *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char fwh_sm[];
+    const int o0 = blockIdx.y * MG, mgt = min(MG, nobs - o0);
+    double *acc = (double *)fwh_sm;                           // [MG][FWH_T]
+    float4 *geo = (float4 *)(acc + (size_t)MG * FWH_T);       // [G][MG][2]
+    float4 *winA = geo + (size_t)G * MG * 2;                  // [G][W]: (L, dQ/dtau)
+    float4 *winB = winA + (size_t)G * W;                      // [G][W]: dL/dtau (16-byte lane stride)
+    int *mlo = (int *)(winB + (size_t)G * W);                 // [G]
+    const int tid = threadIdx.x;
+    const int k = blockIdx.x * FWH_T + tid;
+    const int c = blockIdx.z;
+    const double B = floor((t0 + (double)(blockIdx.x * FWH_T) * dt_obs) / dtau);
+    const float skl = (float)((t0 + (double)k * dt_obs) / dtau - B);
+    const float rc0 = (float)(1.0 / c0);
+    for (int o = 0; o < mgt; ++o) acc[o * FWH_T + tid] = 0.0;
+    const int j0 = c * chunk, j1 = min(npts, j0 + chunk);
+    for (int jb = j0; jb < j1; jb += G) {
+        const int ng = min(G, j1 - jb);
+        __syncthreads(); // the previous group's geometry and windows are no longer read
+        for (int i = tid; i < ng * mgt; i += FWH_T) {
+            const int g = i / mgt, o = i - g * mgt, j = jb + g;
+            const double dx = obs[o0 + o] - xyz[j], dy = obs[nobs + o0 + o] - xyz[npts + j],
+                         dz = obs[2 * nobs + o0 + o] - xyz[2 * npts + j];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz), ir = 1.0 / r;
+            const double e = B - r / (c0 * dtau);
+            const double ef = floor(e);
+            geo[(g * MG + o) * 2] = make_float4((float)(dx * ir), (float)(dy * ir), (float)(dz * ir),
+                                                (float)(area[j] * ir / (4.0 * M_PI)));
+            geo[(g * MG + o) * 2 + 1] = make_float4((float)(e - ef), __int_as_float((int)ef), (float)ir, 0.0f);
+        }
+        __syncthreads();
+        if (tid < ng) { // window start: the earliest frame any microphone needs
+            int m = 0x7fffffff;
+            for (int o = 0; o < mgt; ++o) m = min(m, __float_as_int(geo[(tid * MG + o) * 2 + 1].y));
+            mlo[tid] = max(m, 0);
+        }
+        __syncthreads();
+        for (int i = tid; i < ng * W * 2; i += FWH_T) {
+            const int g = i / (2 * W), r2 = i - g * 2 * W;
+            const int f = min(mlo[g] + (r2 >> 1), N - 1);
+            (r2 & 1 ? winB : winA)[g * W + (r2 >> 1)] = src[((long long)(jb + g) * N + f) * 2 + (r2 & 1)];
+        }
+        __syncthreads();
+        if (k < nt) {
+            for (int o = 0; o < mgt; ++o) {
+                float sum = 0.0f, comp = 0.0f;
+                for (int g = 0; g < ng; ++g) {
+                    const float4 gd = geo[(g * MG + o) * 2], h = geo[(g * MG + o) * 2 + 1];
+                    const float s = skl + h.x;
+                    const float fl = floorf(s);
+                    int m = __float_as_int(h.y) + (int)fl;
+                    m = m < 0 ? 0 : (m > N - 2 ? N - 2 : m);
+                    int idx = m - mlo[g];
+                    idx = idx < 0 ? 0 : (idx > W - 2 ? W - 2 : idx);
+                    const float w = s - fl;
+                    const float4 *pa = winA + g * W + idx, *pb = winB + g * W + idx;
+                    const float4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
+                    const float Lx = fmaf(w, a1.x - a0.x, a0.x), Ly = fmaf(w, a1.y - a0.y, a0.y),
+                                Lz = fmaf(w, a1.z - a0.z, a0.z), dQ = fmaf(w, a1.w - a0.w, a0.w);
+                    const float dLx = fmaf(w, b1.x - b0.x, b0.x), dLy = fmaf(w, b1.y - b0.y, b0.y),
+                                dLz = fmaf(w, b1.z - b0.z, b0.z);
+                    const float Lr = fmaf(Lx, gd.x, fmaf(Ly, gd.y, Lz * gd.z));
+                    const float dLr = fmaf(dLx, gd.x, fmaf(dLy, gd.y, dLz * gd.z));
+                    const float v = gd.w * fmaf(Lr, h.z, fmaf(dLr, rc0, dQ));
+                    const float y = v - comp;
+                    const float tsum = sum + y;
+                    comp = (tsum - sum) - y;
+                    sum = tsum;
+                }
+                acc[o * FWH_T + tid] += (double)sum;
+            }
+        }
+    }
+    if (k < nt)
+        for (int o = 0; o < mgt; ++o) part[((long long)c * nobs + o0 + o) * nt + k] = acc[o * FWH_T + tid];
+}
+
 __global__ void k_fwh_sum(const double *__restrict__ part, int nchunk, long long n, double *__restrict__ out)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -203,17 +296,26 @@ extern "C" int les_fwh(const void *ring, int precision, int capacity, int64_t fr
     const int N = (int)std::min<int64_t>(frames_written, capacity);
     if (frames_written < 3 || N < 3) return bad("at least three frames are needed");
     if (!(dtau > 0) || !(c0 > 0) || !(dt_obs >= 0)) return bad("dtau and c0 must be > 0, dt_obs >= 0");
-    // every emission time of every panel must lie within the frames
+    // every emission time of every panel must lie within the frames; on the
+    // way, the largest spread of a panel's distances over a group of 16
+    // microphones (the window the staged observer pass needs)
     const double tau_max = (N - 1) * dtau, t1 = t0 + (nt - 1) * dt_obs;
+    std::vector<double> gmin((size_t)npts), gmax((size_t)npts);
+    double spread16 = 0.0;
     for (int o = 0; o < nobs; ++o) {
         double rmin = 1e300, rmax = 0.0;
+        const bool g0 = o % 16 == 0;
         for (int j = 0; j < npts; ++j) {
             const double dx = obs[o] - xyz[j], dy = obs[nobs + o] - xyz[npts + j], dz = obs[2 * nobs + o] - xyz[2 * npts + j];
             const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
             if (!(r > 0)) return bad("an observer coincides with a panel");
             rmin = std::min(rmin, r);
             rmax = std::max(rmax, r);
+            gmin[j] = g0 ? r : std::min(gmin[j], r);
+            gmax[j] = g0 ? r : std::max(gmax[j], r);
         }
+        if (o % 16 == 15 || o == nobs - 1)
+            for (int j = 0; j < npts; ++j) spread16 = std::max(spread16, gmax[j] - gmin[j]);
         if (t0 - rmax / c0 < 0.0 || t1 - rmin / c0 > tau_max)
             return bad("an emission time t - r/c0 falls outside the frames: need t0 >= r_max/c0 and "
                        "t0 + (nt-1) dt_obs - r_min/c0 <= (frames - 1) dtau");
@@ -225,10 +327,31 @@ extern "C" int les_fwh(const void *ring, int precision, int capacity, int64_t fr
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LES_ERR_CUDA;
     const int tblocks = (nt + FWH_T - 1) / FWH_T;
-    int nchunk = (4 * nsm + tblocks * nobs - 1) / (tblocks * nobs);
-    nchunk = std::max(1, std::min(nchunk, (npts + FWH_SUB - 1) / FWH_SUB));
-    const int chunk = ((npts + nchunk - 1) / nchunk + FWH_SUB - 1) / FWH_SUB * FWH_SUB;
-    nchunk = (npts + chunk - 1) / chunk;
+    // The staged observer pass (k_fwh_obs_win) with microphone groups of 16:
+    // a window of W frames per panel (the block's 256 times plus the spread of
+    // the group's emission times), G panels per stage within ~100 KB of shared
+    // memory; if fewer than 4 panels fit, the direct pass (k_fwh_obs).
+    const int MG = std::min(16, nobs), ngroups = (nobs + MG - 1) / MG;
+    const double W_d = std::ceil(spread16 / (c0 * dtau)) + std::ceil((FWH_T - 1) * dt_obs / dtau) + 4.0;
+    const int W = W_d < 1e6 ? (int)W_d : 1000000;
+    const size_t budget = 100 * 1024, acc_b = (size_t)MG * FWH_T * 8; // two CTAs per SM
+    const int G = (int)std::min<size_t>(32, (budget - acc_b) / (32 * ((size_t)MG + W) + 4));
+    const bool staged = G >= 4;
+    const size_t win_smem = acc_b + (size_t)G * MG * 32 + (size_t)G * W * 32 + (size_t)G * 4;
+    int nchunk, chunk;
+    if (staged) {
+        nchunk = std::max(1, std::min(npts, (2 * nsm + tblocks * ngroups - 1) / (tblocks * ngroups)));
+        chunk = (npts + nchunk - 1) / nchunk;
+        nchunk = (npts + chunk - 1) / chunk;
+        if (cudaFuncSetAttribute(k_fwh_obs_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem) !=
+            cudaSuccess)
+            return LES_ERR_CUDA;
+    } else {
+        nchunk = (4 * nsm + tblocks * nobs - 1) / (tblocks * nobs);
+        nchunk = std::max(1, std::min(nchunk, (npts + FWH_SUB - 1) / FWH_SUB));
+        chunk = ((npts + nchunk - 1) / nchunk + FWH_SUB - 1) / FWH_SUB * FWH_SUB;
+        nchunk = (npts + chunk - 1) / chunk;
+    }
     const size_t n_src = (size_t)npts * N * 2;
     const size_t n_out = (size_t)nobs * nt;
     float4 *d_src = nullptr;
@@ -268,8 +391,12 @@ extern "C" int les_fwh(const void *ring, int precision, int capacity, int64_t fr
         else
             k_fwh_src<float><<<grid, 256, 0, st>>>((const float *)ring, first, capacity, npts, N, d_nrm, p0, rdt2, d_src);
         if (ms_out) cudaEventRecord(ev[1], st);
-        k_fwh_obs<<<dim3(tblocks, nobs, nchunk), FWH_T, 0, st>>>(d_src, npts, N, d_xyz, d_area, d_obs, nobs, t0,
-                                                                 dt_obs, nt, dtau, c0, chunk, d_part);
+        if (staged)
+            k_fwh_obs_win<<<dim3(tblocks, ngroups, nchunk), FWH_T, win_smem, st>>>(
+                d_src, npts, N, d_xyz, d_area, d_obs, nobs, MG, t0, dt_obs, nt, dtau, c0, chunk, G, W, d_part);
+        else
+            k_fwh_obs<<<dim3(tblocks, nobs, nchunk), FWH_T, 0, st>>>(d_src, npts, N, d_xyz, d_area, d_obs, nobs, t0,
+                                                                     dt_obs, nt, dtau, c0, chunk, d_part);
         if (ms_out) cudaEventRecord(ev[2], st);
         k_fwh_sum<<<(int)((n_out + 255) / 256), 256, 0, st>>>(d_part, nchunk, (long long)n_out, d_out);
         if (cudaGetLastError() != cudaSuccess ||

@@ -1,6 +1,7 @@
 """FW-H far-field pressure on the GPU (les_fwh) against the oracle
 (oracle/fwh.py) element by element: on the exact field of a point monopole
-(either ring precision, a wrapped ring), on the probe frames of an LES jet
+(either ring precision, a wrapped ring; the staged observer pass and, for
+observer times far apart, the direct one), on the probe frames of an LES jet
 run (real flow through the surface, so the quadratic momentum-flux term
 counts), bit-identical reruns, and the refused inputs."""
 import numpy as np
@@ -88,6 +89,21 @@ def test_monopole_against_the_oracle_and_the_exact_field(prec):
     t = t0 + dt_obs * np.arange(nt) + (nfr - cap) * dtau
     exact = np.stack([_monopole(obs[:, o:o + 1], t)[0] for o in range(obs.shape[1])])
     assert np.abs(got - exact).max() <= 5e-3 * np.abs(exact).max()
+
+
+def test_sparse_observer_times_take_the_direct_pass():
+    """Observer times far apart (a window of frames per panel too long to
+    stage in shared memory): the direct observer pass, against the oracle."""
+    import torch
+    xyz, nrm, area = _sphere(1.0, 24, 48)
+    dtau, nfr = 0.01, 1400
+    frames = _frames(xyz, nfr, dtau)
+    ring = _ring(frames, nfr, torch.float64)
+    obs = np.array([[6.0, 0.0, 0.0]]).T
+    t0, dt_obs, nt = 8.8, 0.9, 6                 # 90 frames between observer times
+    got = les.les_fwh(ring.data_ptr(), les.LES_FP64, nfr, nfr, xyz, nrm, area, dtau, P0, C0, obs, t0, dt_obs, nt)
+    ref = fwh.pressure(frames, xyz, nrm, area, dtau, RHO0, P0, C0, obs, t0, dt_obs, nt)
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
 def test_reruns_are_bit_identical_and_bad_inputs_refused():
