@@ -308,9 +308,10 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     real w[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) w[b] = mr[0] * D[0][b] + mr[1] * D[1][b] + mr[2] * D[2][b];
-    real tr = real(0);
+    // one multiply-add chain over the nine products (no zero start)
+    real tr = Ab[0] * D[0][0];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) tr += Ab[i] * D[i][0] + Ab[3 + i] * D[i][1] + Ab[6 + i] * D[i][2];
+    for (int t = 1; t < 9; ++t) tr = fma(Ab[3 * (t % 3) + t / 3], D[t / 3][t % 3], tr);
     const real coef = (G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]) * jb; // 2 x average x J^-1
     const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]) * jb;
     const real ch = real(0.5) * coef, ct = coef * tr * real(1.0 / 3.0);
@@ -391,9 +392,9 @@ __global__ void __launch_bounds__(BLOCK) k_update(const JetDev<real> *__restrict
         real R[5];
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
-            real acc = real(0);
+            real acc = Hf[f * fs + lp] - Hf[f * fs + back[0]];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc += Hf[(5 * a + f) * fs + lp] - Hf[(5 * a + f) * fs + back[a]];
+            for (int a = 1; a < 3; ++a) acc += Hf[(5 * a + f) * fs + lp] - Hf[(5 * a + f) * fs + back[a]];
             R[f] = acc;
         }
         if (rhs_only) {
