@@ -36,9 +36,11 @@ from paper_2212_12365_gb300 import inputs as I  # noqa: E402
 # divide/sqrt = 1, min/max/abs = 0): point pass 94 (the 5 multiplications of
 # the J^-1 Q scaling included; primitives, Sutherland, spectral radii and
 # lambda-bar, half point fluxes), gradients and closures 112, three interface
-# fluxes 3 x 158 = 474, update 35.  The FP32 fused stage does the same work
-# less the scaling and plus one J multiplication in the update: 711.
-FLOPS_PER_PT_STAGE = {"point": 94, "grads": 112, "iface": 474, "update": 35}
+# fluxes 3 x 155 = 465 (the 1/2 of the interface averages of lambda-bar, mu_eff
+# and kappa sits in the stored half interface J^-1), update 35: 706.  The FP32
+# fused stage does the same work less the scaling, plus one J multiplication
+# in the update and those three 1/2 factors per interface: 711.
+FLOPS_PER_PT_STAGE = {"point": 94, "grads": 112, "iface": 465, "update": 35}
 FLOPS_PER_PT_STAGE_FUSED = 711
 # Algorithmic HBM bytes per point and stage: stages 2-5 read Q(l-1), Q(0) and 10
 # metric values and write Q(l); stage 1 reads Q(0) once: 24 values on average.
@@ -54,8 +56,8 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
 _PAPER_JET = "jet-384x256x144"
 KERNEL_SOURCE = {"k_iface": "les_stage.cu", "k_fused": "les_fused.cu"}
 TRAFFIC_BYTES_PER_POINT = {  # (workload, precision, kernel, decomposition) -> (bytes per point, source sha16)
-    # profiles/stage_kernels_fp64_jet-384x256x144.md: 13431.0 + 1682.2 MB per launch
-    (_PAPER_JET, "fp64", "k_iface", None): (1067.64, "fb880ab93d8e0603"),
+    # profiles/stage_kernels_fp64_jet-384x256x144.md: 13410.7 + 1682.1 MB per launch
+    (_PAPER_JET, "fp64", "k_iface", None): (1066.19, "f5518e02ae9e3898"),
     # profiles/fused_stage_fp32_jet-384x256x144.md and ..._separable_...
     (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.45, "37b78006e805df85"),
     (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.56, "37b78006e805df85"),
@@ -98,8 +100,8 @@ def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str,
 # the source hash of the captured kernel as above
 PIPE_UTIL_NCU = {  # (precision, kernel) -> (metrics dict, source sha16)
     # profiles/stage_kernels_fp64_jet-384x256x144.md (192x128x72 capture)
-    ("fp64", "k_iface"): ({"fp64_pipe_pct": 87.90, "executed_fp64_flop_per_point": 469.7,
-                          "dadd_dmul_dfma_per_point": [132.8, 85.2, 125.9]}, "fb880ab93d8e0603"),
+    ("fp64", "k_iface"): ({"fp64_pipe_pct": 88.58, "executed_fp64_flop_per_point": 459.8,
+                          "dadd_dmul_dfma_per_point": [121.9, 70.4, 133.8]}, "f5518e02ae9e3898"),
     # profiles/fused_stage_fp32_jet-384x256x144.md (192x128x72 capture, 32x16 tiles)
     ("fp32", "k_fused"): ({"fma_pipe_pct": 32.0, "fmaheavy_pct": 32.3, "fmalite_pct": 31.0, "issue_active_pct": 37.6,
                           "executed_fp32_flop_per_point": 1316.9, "thread_instructions_per_point": 1187.4},

@@ -17,8 +17,9 @@ namespace les {
 constexpr int NF = 5;         // conserved variables
 // Static per-point grid fields (computed once in FP64, stored in the state
 // precision): the nine metric cofactors J^-1 d xi^a / d x_c at [3a + c],
-// J^-1, (Cs Delta)^2, J, and per axis a: the J^-1 average of the interface
-// to the +a neighbour, its reciprocal, and |row a| = sqrt(sum_c m_ac^2).
+// J^-1, (Cs Delta)^2, J, and per axis a: half the J^-1 average of the
+// interface to the +a neighbour, the reciprocal of that average (not halved),
+// and |row a| = sqrt(sum_c m_ac^2).
 constexpr int NMET = 21;      // fields of every precision
 constexpr int MET_A0 = 21;    // FP64 only: 27 interface tables, see below
 constexpr int MET_K0 = 48;    // FP64 only: 9 interface contractions, see below

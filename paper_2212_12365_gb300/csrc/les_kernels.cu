@@ -186,7 +186,9 @@ __global__ void __launch_bounds__(BLOCK) k_static_fields(double *met, long long 
             else if (q[a] + 1 < n[a]) r[a] = q[a] + 1;
             const long long oR = ((long long)r[2] * nj + r[1]) * pitch + r[0];
             const double jb = 0.5 * (jinv + met[MET_JINV * fs + oR]);
-            met[(MET_JB + a) * fs + o] = jb;
+            // stored halved: the interface flux wants 1/2 (sum of the two
+            // points' coefficients) times J^-1, so the 1/2 is taken here once
+            met[(MET_JB + a) * fs + o] = 0.5 * jb;
             // an interface along the degenerate axis has no volume: zero weights
             met[(MET_RJB + a) * fs + o] = jb > 0.0 ? 1.0 / jb : 0.0;
             const double mx = met[(3 * a) * fs + o], my = met[(3 * a + 1) * fs + o],

@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(BLOCK) k_grads(const JetDev<real> *__restrict_
             const real pm = P[P_P * fs + lidx(J, rm[0], rm[1], rm[2])];
             const real p0 = P[P_P * fs + lidx(J, r0[0], r0[1], r0[2])];
             const real pp = P[P_P * fs + lidx(J, rp[0], rp[1], rp[2])];
-            G[(G_NU + a) * fs + lp] = fabs(pp - real(2) * p0 + pm) * rcp1_<real>(pp + real(2) * p0 + pm);
+            const real ps = pp + pm;
+            G[(G_NU + a) * fs + lp] = fabs(fma(real(-2), p0, ps)) * rcp1_<real>(fma(real(2), p0, ps));
         }
 #pragma unroll
         for (int f = 0; f < 4; ++f)
@@ -253,8 +254,8 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     // scaled by the interface lambda-bar and J^-1
     const real eps2 = (real)J.k2 * fmax(G[(G_NU + a) * fs + L], G[(G_NU + a) * fs + R]);
     const real eps4 = fmax(real(0), (real)J.k4 - eps2);
-    const real jb = M[(MET_JB + a) * fs + L];
-    const real sc = jb * real(0.5) * (P[(P_LXI + a) * fs + L] + P[(P_LXI + a) * fs + R]);
+    const real jbh = M[(MET_JB + a) * fs + L]; // half the interface J^-1
+    const real sc = jbh * (P[(P_LXI + a) * fs + L] + P[(P_LXI + a) * fs + R]);
     const real se4 = sc * eps4;
     // se2 dW - se4 (dW(+3/2) - 2 dW(+1/2) + dW(-1/2)) with the third
     // difference written as W(R+1) - W(L-1) - 3 dW(+1/2): the flux gains
@@ -296,7 +297,7 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     for (int t = 0; t < 3; ++t) K[t] = M[(MET_K0 + 3 * a + t) * fs + L];
     const real *mr = Ab + 3 * a; // averaged cofactor row a / interface J^-1
     // The flux needs only the row-a contraction of the stress tensor,
-    //   s_i = sum_c mr_c tau_ci = coef (1/2 (X_i + Y_i) - mr_i tr/3),
+    //   s_i = sum_c mr_c tau_ci = ch (X_i + Y_i - 2/3 mr_i tr), ch = mu_eff J^-1,
     // with X_i = sum_c mr_c du_i/dx_c = sum_b K_b D_ib,
     //      Y_i = sum_c mr_c du_c/dx_i = sum_b Ab_bi (sum_c mr_c D_cb),
     //      tr  = div u = sum_i sum_b Ab_bi D_ib,
@@ -312,9 +313,10 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
     real tr = Ab[0] * D[0][0];
 #pragma unroll
     for (int t = 1; t < 9; ++t) tr = fma(Ab[3 * (t % 3) + t / 3], D[t / 3][t % 3], tr);
-    const real coef = (G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]) * jb; // 2 x average x J^-1
-    const real kap = real(0.5) * (G[G_KAP * fs + L] + G[G_KAP * fs + R]) * jb;
-    const real ch = real(0.5) * coef, ct = coef * tr * real(1.0 / 3.0);
+    // interface averages of mu_eff and kappa times J^-1: the sums times jbh
+    const real ch = (G[G_MUEFF * fs + L] + G[G_MUEFF * fs + R]) * jbh;
+    const real kap = (G[G_KAP * fs + L] + G[G_KAP * fs + R]) * jbh;
+    const real ct = ch * tr * real(2.0 / 3.0);
     real sv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
