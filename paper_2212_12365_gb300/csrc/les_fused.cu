@@ -1061,9 +1061,41 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 const bool updA = !first && outA && kU >= k0, updB = !first && outB && kU >= k0;
                 const long long pU = (long long)gkU * plane;
                 const long long oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
+                // zeta: R = the own column one plane up; R + 1 two planes up;
+                // L - 1 one plane down (carried, or read on the first plane).
+                // General form: evaluated in the same block as the xi and eta
+                // fluxes (independent work for the scheduler to interleave)
+                auto zeta = [&]() {
+                    const Pts R = pts(CK_RING(sUp + c2));
+                    float2 WR[5], WRp[5];
+                    wvec(R, WR);
+                    if (ghost_hi) {
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) WRp[f] = WL[f]; // W(nk) = W(nk - 2)
+                    } else {
+                        wof(CK_RING(sUpp + c2), WRp);
+                    }
+                    Side SL, SR;
+                    side(2, rU, c1, SL);
+                    side(2, rP, c1, SR);
+                    if constexpr (SEP) {
+                        const float2 Sa = mul2(bc(hXo.x), hYo);
+                        const float2 hb = bc(0.5f * (hZo.x + hZp.x));
+                        iface_sep<2>(FP, L, WL, R, WR, Wc, WRp, SL, SR, Sa, hb, rcp2(hb), bc(0.25f * hXo.y),
+                                     mul2(bc(0.25f), rhYo), hz);
+                    } else {
+                        float2 mR[9], jR;
+                        mets(mP, c1, mR, jR);
+                        iface<2>(FP, L, WL, mL, jL, R, WR, mR, jR, Wc, WRp, SL, SR, hz);
+                    }
+                };
                 if (!first) {
-                    // xi: R = the next column (lanes 0..30; lane 31's R has no R1 data)
-                    if (tx <= FX - 2) {
+                    // xi: R = the next column.  Lane 31's R has no R1 data: it pairs
+                    // with its own R1 cell (an unused result), so that every lane
+                    // runs the xi flux without a branch and the scheduler can
+                    // interleave it with the eta flux
+                    {
+                        const int cR = tx <= FX - 2 ? c1 + 1 : c1;
                         const Pts R = pts(CK_RING(sU + c2 + 1));
                         float2 WR[5], WRp[5], WLm[5];
                         wvec(R, WR);
@@ -1071,7 +1103,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                         wof(CK_RING(sU + c2 - 1), WLm);
                         Side SL, SR;
                         side(0, rU, c1, SL);
-                        side(0, rU, c1 + 1, SR);
+                        side(0, rU, cR, SR);
                         if constexpr (SEP) {
                             // Sa = h_y h_z, hb = average h_x, tangential 1/(4 h)
                             const float2 Sa = mul2(hYo, bc(hZo.x));
@@ -1080,7 +1112,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                                          mul2(bc(0.25f), rhYo), bc(0.25f * hZo.y), hx);
                         } else {
                             float2 mR[9], jR;
-                            mets(mU, c1 + 1, mR, jR);
+                            mets(mU, cR, mR, jR);
                             iface<0>(FP, L, WL, mL, jL, R, WR, mR, jR, WLm, WRp, SL, SR, hx);
                         }
                     }
@@ -1127,33 +1159,11 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     }
 #pragma unroll
                     for (int f = 0; f < 5; ++f) S.SH[CK_SH(f * NT + tid)] = hy[f].y;
+                    if constexpr (!SEP) zeta();
+                } else if constexpr (!SEP) {
+                    zeta();
                 }
-                // zeta: R = the own column one plane up; R + 1 two planes up;
-                // L - 1 one plane down (carried, or read on the first plane)
-                {
-                    const Pts R = pts(CK_RING(sUp + c2));
-                    float2 WR[5], WRp[5];
-                    wvec(R, WR);
-                    if (ghost_hi) {
-#pragma unroll
-                        for (int f = 0; f < 5; ++f) WRp[f] = WL[f]; // W(nk) = W(nk - 2)
-                    } else {
-                        wof(CK_RING(sUpp + c2), WRp);
-                    }
-                    Side SL, SR;
-                    side(2, rU, c1, SL);
-                    side(2, rP, c1, SR);
-                    if constexpr (SEP) {
-                        const float2 Sa = mul2(bc(hXo.x), hYo);
-                        const float2 hb = bc(0.5f * (hZo.x + hZp.x));
-                        iface_sep<2>(FP, L, WL, R, WR, Wc, WRp, SL, SR, Sa, hb, rcp2(hb), bc(0.25f * hXo.y),
-                                     mul2(bc(0.25f), rhYo), hz);
-                    } else {
-                        float2 mR[9], jR;
-                        mets(mP, c1, mR, jR);
-                        iface<2>(FP, L, WL, mL, jL, R, WR, mR, jR, Wc, WRp, SL, SR, hz);
-                    }
-                }
+                if constexpr (SEP) zeta();
                 // the -1/2 xi flux from the lane below (all lanes of the warp
                 // take part in the shuffle; the CTA-uniform `first` guards it)
                 float2 hxm[5];
