@@ -708,10 +708,30 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 const float2 r = rcp2(den);
                 return make_float2(fabsf(num.x) * r.x, fabsf(num.y) * r.y);
             };
+            // Separable form: derivatives and sensor along xi or zeta in one
+            // instruction sequence for every lane, from the cells o1, o2 and the
+            // own cell with selected weights: central (t = 0: o1, o2 = c -+ 1,
+            // weights 0, -1, 1; sensor over o1, c, o2) or one-sided (o1, o2 =
+            // c + t, c + 2t, weights -3t, 4t, -t; sensor over c, o1, o2).  The
+            // same values as the branches of the general form below, which keeps
+            // the branches (its register budget is tighter; both measured).
+            auto axis3 = [&](int o1, int o2, int t, float2 dd[4], float2 &nn) {
+                const float4 a1 = S.PA[o1], b1 = S.PB[o1], q1 = S.PC[o1];
+                const float4 a2 = S.PA[o2], b2 = S.PB[o2], q2 = S.PC[o2];
+                const float tf = (float)t;
+                const float2 w0 = bc(-3.0f * tf), w1 = bc(t == 0 ? -1.0f : 4.0f * tf), w2 = bc(t == 0 ? 1.0f : -tf);
+                dd[0] = fma2(w2, hi2(a2), fma2(w1, hi2(a1), mul2(w0, U0[0])));
+                dd[1] = fma2(w2, lo2(b2), fma2(w1, lo2(b1), mul2(w0, U0[1])));
+                dd[2] = fma2(w2, hi2(b2), fma2(w1, hi2(b1), mul2(w0, U0[2])));
+                dd[3] = fma2(w2, hi2(q2), fma2(w1, hi2(q1), mul2(w0, T0)));
+                nn = sensor(t == 0 ? lo2(q1) : p0, t == 0 ? p0 : lo2(q1), lo2(q2));
+            };
             // along xi: central, or one-sided over the cells c, c+t, c+2t at a
             // non-periodic end (the sensor of an end point is its interior
             // neighbour's: same three points)
-            if (ti == 0) {
+            if constexpr (SEP) {
+                axis3(CK_RING(s0 + c2 + (ti == 0 ? -1 : ti)), CK_RING(s0 + c2 + (ti == 0 ? 1 : 2 * ti)), ti, d[0], nu[0]);
+            } else if (ti == 0) {
                 const int om = CK_RING(s0 + c2 - 1), op = CK_RING(s0 + c2 + 1);
                 const float4 am = S.PA[om], bm = S.PB[om], qm = S.PC[om];
                 const float4 ap = S.PA[op], bp = S.PB[op], qp = S.PC[op];
@@ -780,7 +800,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             // at an end of a non-periodic k axis
             {
                 const int tk = (!pk && gk == 0) ? 1 : ((!pk && gk == nk - 1) ? -1 : 0);
-                if (tk == 0) {
+                if constexpr (SEP) {
+                    axis3(CK_RING(rslot<NRING>(tk == 0 ? kg - 1 : kg + tk) * N2 + c2),
+                          CK_RING(rslot<NRING>(tk == 0 ? kg + 1 : kg + 2 * tk) * N2 + c2), tk, d[2], nu[2]);
+                } else if (tk == 0) {
                     const int om = CK_RING(rslot<NRING>(kg - 1) * N2 + c2), op = CK_RING(rslot<NRING>(kg + 1) * N2 + c2);
                     const float4 am = S.PA[om], bm = S.PB[om], qm = S.PC[om];
                     const float4 ap = S.PA[op], bp = S.PB[op], qp = S.PC[op];
@@ -1063,7 +1086,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 const long long oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
                 // zeta: R = the own column one plane up; R + 1 two planes up;
                 // L - 1 one plane down (carried, or read on the first plane).
-                // General form: evaluated in the same block as the xi and eta
+                // General form: evaluated first in the block of the xi and eta
                 // fluxes (independent work for the scheduler to interleave)
                 auto zeta = [&]() {
                     const Pts R = pts(CK_RING(sUp + c2));
@@ -1090,6 +1113,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     }
                 };
                 if (!first) {
+                    if constexpr (!SEP) zeta();
                     // xi: R = the next column.  Lane 31's R has no R1 data: it pairs
                     // with its own R1 cell (an unused result), so that every lane
                     // runs the xi flux without a branch and the scheduler can
@@ -1159,7 +1183,6 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     }
 #pragma unroll
                     for (int f = 0; f < 5; ++f) S.SH[CK_SH(f * NT + tid)] = hy[f].y;
-                    if constexpr (!SEP) zeta();
                 } else if constexpr (!SEP) {
                     zeta();
                 }
