@@ -147,7 +147,8 @@ size_t les_workspace_bytes(const les_grid_desc *g);
  * On success *out owns all device memory of the solver until les_destroy.
  * Errors: LES_ERR_ARG (dims < 4, inconsistent periodic/BC flags, a periodic
  * axis in the overlapping form, INFLOW_JET
- * off the i- face, mach_j <= 0 with INFLOW_JET, non-positive J^-1),
+ * off the i- face, mach_j <= 0 with INFLOW_JET, non-positive J^-1, an FP32
+ * grid of 2^31 / 5 or more padded points: nk x nj x ni rounded up to 32),
  * LES_ERR_OOM, LES_ERR_CUDA. */
 int les_create_grid(const les_grid_desc *g, const les_params *p, void *stream, les_handle **out);
 

@@ -1,6 +1,7 @@
 // Host runtime of libles.so: handles, device memory plan, CUDA-graph step,
 // state transfer, diagnostics and the surface probe behind the C ABI of les.h.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -148,6 +149,8 @@ static int wait_status(les_handle *h)
 // Validation and memory plan
 // ---------------------------------------------------------------------------
 
+static void plan_jet(const les_grid_desc *g, int prec, JetHost &J);
+
 static std::string validate(const les_grid_desc *g, const les_params *p)
 {
     if (!g || !p) return "null descriptor or parameters";
@@ -155,6 +158,16 @@ static std::string validate(const les_grid_desc *g, const les_params *p)
     if (!g->x || !g->y || !g->z) return "null coordinate array";
     if (g->precision != LES_FP64 && g->precision != LES_FP32 && g->precision != LES_FP32_SEPARABLE)
         return "unknown precision";
+    if (g->precision != LES_FP64) {
+        // the fused FP32 stage addresses the five fields of a register and the
+        // static records with 32-bit offsets
+        JetHost J;
+        plan_jet(g, LES_FP32, J);
+        const long long rec = (long long)g->nk * ((g->nj + 1) / 2) * 5 * J.pitch;
+        if (5 * J.fs > INT_MAX || rec > INT_MAX)
+            return "FP32 grid too large: 5 x padded points (" + std::to_string(5 * J.fs) +
+                   ") must stay below 2^31";
+    }
     for (int a = 0; a < 3; ++a) {
         bool pf = g->face_bc[2 * a] == LES_BC_PERIODIC, pb = g->face_bc[2 * a + 1] == LES_BC_PERIODIC;
         if (g->periodic[a] != 0 && g->periodic[a] != 1) return "periodic flags must be 0/1";

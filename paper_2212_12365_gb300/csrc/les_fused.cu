@@ -572,8 +572,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         }
         const int i0 = ilo + bx * (FX - 2), j0 = jlo + by * (TY - 2);
         const int ib = i0 - 1, jb = j0 - 1; // grid column / row of the tile's first R1 cell (jb even)
-        const long long fs = J.fs;
-        const long long plane = (long long)nj * J.pitch;
+        // 32-bit offsets: creation limits an FP32 jet to 5 fields x fs and its
+        // static records to fewer than 2^31 elements
+        const int fs = (int)J.fs;
+        const int plane = nj * J.pitch;
         const float *__restrict__ Qs = J.q[src];
         float *__restrict__ Qd = J.q[dst];
         const float adt = rhs_only ? 0.0f : c_alpha_f[stage] * (float)dt[jet];
@@ -600,14 +602,14 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         const bool col_out = tx >= 1 && tx <= FX - 2 && (ib + tx) < ihi;
         const bool outA = col_out && rA >= 1 && rA <= TY - 2 && (jb + rA) < jhi;
         const bool outB = col_out && rB >= 1 && rB <= TY - 2 && (jb + rB) < jhi;
-        const long long ocolA = (long long)gjA * J.pitch + gi, ocolB = (long long)gjB * J.pitch + gi;
+        const int ocolA = gjA * J.pitch + gi, ocolB = gjB * J.pitch + gi;
         // slots of the two rows' Q(0) values in QZ (outputs only)
         const int zA = (rA - 1) * (FX - 2) + (tx - 1), zB = (rB - 1) * (FX - 2) + (tx - 1);
         // the R2 pair cells this thread loads (at most two) and, per row, the
         // offset of its source point in the staging box and in a plane
         int lc[2];
         int bo[2][2];
-        long long go[2][2];
+        int go[2][2];
         const CUtensorMap *tmap = nullptr;
         int tx0 = 0;
         if (F.tmap && tma_smem_ok && !pi && !pj && !tma_off) {
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int gr = map_idx(jb + 2 * (pr - 1) + h, nj, pj);
-                go[t][h] = (long long)gr * J.pitch + gc;
+                go[t][h] = gr * J.pitch + gc;
                 int rr = gr - (jb - 2), cl = gc - tx0;
                 rr = rr < 0 ? 0 : (rr > BR - 1 ? BR - 1 : rr);
                 cl = cl < 0 ? 0 : (cl > TMA_BOX_X - 1 ? TMA_BOX_X - 1 : cl);
@@ -667,17 +669,17 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         auto fetch_met = [&](int kg) {
             const int gk = map_idx(kg, nk, pk);
             float4 *dst = S.MA + CK_TAB((r3(kg) * 5) * N1 + c1, 15 * N1);
-            const long long rp = J.pitch;
+            const int rp = J.pitch;
             if (!rec_split) {
-                const long long r0 = ((long long)gk * F.njp + jpA) * 5 * rp + gi;
+                const int r0 = (gk * F.njp + jpA) * 5 * rp + gi;
                 const float4 *p = mp + CK_G(3, r0, nrec);
                 (void)CK_G(3, r0 + 4 * rp, nrec);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) cp_async16(dst + q * N1, p + q * rp);
             } else {
                 // rows from two records: take each row's lane
-                const long long ra = ((long long)gk * F.njp + (gjA >> 1)) * 5 * rp + gi;
-                const long long rb = ((long long)gk * F.njp + (gjB >> 1)) * 5 * rp + gi;
+                const int ra = (gk * F.njp + (gjA >> 1)) * 5 * rp + gi;
+                const int rb = (gk * F.njp + (gjB >> 1)) * 5 * rp + gi;
                 const float4 *pa = mp + CK_G(3, ra, nrec);
                 const float4 *pb = mp + CK_G(3, rb, nrec);
                 (void)CK_G(3, ra + 4 * rp, nrec);
@@ -976,7 +978,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     }
                 }
                 const int sb = rslot<NRING>(kL) * N2;
-                const long long pofs = (long long)gkL * plane;
+                const int pofs = gkL * plane;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (lc[t] < 0) continue;
@@ -988,7 +990,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                             for (int f = 0; f < 5; ++f)
                                 q[h][f] = S.QG[CK_TAB(f * (BR * TMA_BOX_X) + bo[t][h], 5 * BR * TMA_BOX_X)];
                         } else {
-                            const long long o = CK_G(2, pofs + go[t][h], J.npts_pad);
+                            const int o = CK_G(2, pofs + go[t][h], J.npts_pad);
 #pragma unroll
                             for (int f = 0; f < 5; ++f) q[h][f] = Qs[f * fs + o];
                         }
@@ -1028,15 +1030,15 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 if (tid == 0) cp_async16(S.HZ + ((kL + 1) & 3), F.h1[2] + map_idx(kL + 1, nk, pk));
             }
             if (!rhs_only && kL - 2 >= k0 && kL - 2 <= k1 - 1) {
-                const long long pU = (long long)map_idx(kL - 2, nk, pk) * plane;
+                const int pU = map_idx(kL - 2, nk, pk) * plane;
                 const float *Q0 = J.q[0];
                 if (outA) {
-                    const long long oA = CK_G(4, pU + ocolA, J.npts_pad);
+                    const int oA = CK_G(4, pU + ocolA, J.npts_pad);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) cp_async4(S.QZ + CK_TAB(f * G_::QZN + zA, 5 * G_::QZN), Q0 + f * fs + oA);
                 }
                 if (outB) {
-                    const long long oB = CK_G(4, pU + ocolB, J.npts_pad);
+                    const int oB = CK_G(4, pU + ocolB, J.npts_pad);
 #pragma unroll
                     for (int f = 0; f < 5; ++f) cp_async4(S.QZ + CK_TAB(f * G_::QZN + zB, 5 * G_::QZN), Q0 + f * fs + oB);
                 }
@@ -1082,8 +1084,8 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     hz[f] = bc(0.0f);
                 }
                 const bool updA = !first && outA && kU >= k0, updB = !first && outB && kU >= k0;
-                const long long pU = (long long)gkU * plane;
-                const long long oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
+                const int pU = gkU * plane;
+                const int oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
                 // zeta: R = the own column one plane up; R + 1 two planes up;
                 // L - 1 one plane down (carried, or read on the first plane).
                 // General form: evaluated first in the block of the xi and eta

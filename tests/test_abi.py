@@ -85,6 +85,9 @@ def _desc(spec, **over):
     ({"precision": 7}, {}),
     ({}, {"gamma": 1.0}),
     ({}, {"Re": -1.0}),
+    # an FP32 grid whose five fields need offsets of 2^31 or more (checked
+    # before any coordinate is read)
+    ({"ni": 1024, "nj": 1024, "nk": 512, "precision": 1}, {}),
 ])
 def test_invalid_descriptors_rejected_without_gpu(lib, over, pover):
     from paper_2212_12365_gb300 import les
