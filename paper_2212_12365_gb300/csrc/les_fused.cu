@@ -663,12 +663,11 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         const int kfirst = k0 - 2, klast = k1 + 1;
         if (tmap) stage_box(kfirst);
 
-        // ---- metric cofactors and J^-1 of plane kg for the own row pair (general
-        //      form) into MA[r3(kg)]: asynchronous copies, waited for one plane
-        //      later; where the two rows come from two records, plain loads ----
-        auto fetch_met = [&](int kg) {
-            const int gk = map_idx(kg, nk, pk);
-            float4 *dst = S.MA + CK_TAB((r3(kg) * 5) * N1 + c1, 15 * N1);
+        // ---- metric cofactors and J^-1 of grid plane gk for the own row pair
+        //      (general form) into MA slot q3: asynchronous copies, waited for one
+        //      plane later; where the two rows come from two records, plain loads ----
+        auto fetch_met = [&](int gk, int q3) {
+            float4 *dst = S.MA + CK_TAB((q3 * 5) * N1 + c1, 15 * N1);
             const int rp = J.pitch;
             if (!rec_split) {
                 const int r0 = (gk * F.njp + jpA) * 5 * rp + gi;
@@ -693,10 +692,14 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             }
         };
 
-        // ---- gradients, closures, sensors, lambda-bar of plane kg (own pair) ----
-        auto grad = [&](int kg) {
-            const int gk = map_idx(kg, nk, pk);
-            const int s0 = rslot<NRING>(kg) * N2;
+        // ---- gradients, closures, sensors, lambda-bar of plane kg (grid plane gk;
+        //      three-plane ring slots q3, q3m, q3p of planes kg, kg - 1, kg + 1) ----
+        auto grad = [&](int kg, int gk, int q3, int q3m, int q3p) {
+            // ring slots of planes kg, kg - 1 (= kg + 2), kg + 1 (= kg - 2)
+            const int sl0 = NRING == 4 ? (kg & 3) : q3;
+            const int slm = NRING == 4 ? ((kg - 1) & 3) : q3m, slp = NRING == 4 ? ((kg + 1) & 3) : q3p;
+            const int slm2 = NRING == 4 ? ((kg - 2) & 3) : q3p, slp2 = NRING == 4 ? ((kg + 2) & 3) : q3m;
+            const int s0 = sl0 * N2;
             const int slot = kg & 1;
             const int own = CK_RING(s0 + c2);
             const float4 a0 = S.PA[own], b0 = S.PB[own], q0 = S.PC[own];
@@ -803,10 +806,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             {
                 const int tk = (!pk && gk == 0) ? 1 : ((!pk && gk == nk - 1) ? -1 : 0);
                 if constexpr (SEP) {
-                    axis3(CK_RING(rslot<NRING>(tk == 0 ? kg - 1 : kg + tk) * N2 + c2),
-                          CK_RING(rslot<NRING>(tk == 0 ? kg + 1 : kg + 2 * tk) * N2 + c2), tk, d[2], nu[2]);
+                    axis3(CK_RING((tk == 0 ? slm : (tk > 0 ? slp : slm)) * N2 + c2),
+                          CK_RING((tk == 0 ? slp : (tk > 0 ? slp2 : slm2)) * N2 + c2), tk, d[2], nu[2]);
                 } else if (tk == 0) {
-                    const int om = CK_RING(rslot<NRING>(kg - 1) * N2 + c2), op = CK_RING(rslot<NRING>(kg + 1) * N2 + c2);
+                    const int om = CK_RING(slm * N2 + c2), op = CK_RING(slp * N2 + c2);
                     const float4 am = S.PA[om], bm = S.PB[om], qm = S.PC[om];
                     const float4 ap = S.PA[op], bp = S.PB[op], qp = S.PC[op];
                     d[2][0] = sub2(hi2(ap), hi2(am));
@@ -815,7 +818,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     d[2][3] = sub2(hi2(qp), hi2(qm));
                     nu[2] = sensor(lo2(qm), p0, lo2(qp));
                 } else {
-                    const int o1 = CK_RING(rslot<NRING>(kg + tk) * N2 + c2), o2 = CK_RING(rslot<NRING>(kg + 2 * tk) * N2 + c2);
+                    const int o1 = CK_RING((tk > 0 ? slp : slm) * N2 + c2), o2 = CK_RING((tk > 0 ? slp2 : slm2) * N2 + c2);
                     const float4 a1 = S.PA[o1], b1 = S.PB[o1], q1 = S.PC[o1];
                     const float4 a2 = S.PA[o2], b2 = S.PB[o2], q2 = S.PC[o2];
                     const float2 w0 = bc(-3.0f * tk), w1 = bc(4.0f * tk), w2 = bc(-1.0f * tk);
@@ -846,7 +849,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             } else {
                 float4 u[5];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) u[q] = S.MA[CK_TAB((r3(kg) * 5 + q) * N1 + c1, 15 * N1)];
+                for (int q = 0; q < 5; ++q) u[q] = S.MA[CK_TAB((q3 * 5 + q) * N1 + c1, 15 * N1)];
                 m[0] = lo2(u[0]); m[1] = hi2(u[0]); m[2] = lo2(u[1]); m[3] = hi2(u[1]);
                 m[4] = lo2(u[2]); m[5] = hi2(u[2]); m[6] = lo2(u[3]); m[7] = hi2(u[3]);
                 m[8] = lo2(u[4]);
@@ -953,6 +956,11 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
         };
         for (int kL = kfirst; kL <= klast; ++kL) {
             const int kG = kL - 1, kU = kL - 2;
+            // slots of planes kL, kG, kU in the three-plane rings, and their
+            // grid planes
+            const int q3L = r3(kL), q3G = q3L == 0 ? 2 : q3L - 1, q3U = q3L == 2 ? 0 : q3L + 1;
+            const int gkLm = map_idx(kL, nk, pk), gkGm = map_idx(kG, nk, pk), gkUm = map_idx(kU, nk, pk);
+            const int sLr = NRING == 4 ? (kL & 3) : q3L, sGr = NRING == 4 ? (kG & 3) : q3G, sUr = NRING == 4 ? (kU & 3) : q3U;
             const bool do_grad = kG >= k0 - 1 && kG <= k1 && !(!pk && kG == 0);
             // the first plane of a non-periodic k axis: formed with plane 1
             const bool do_grad0 = !pk && kG == 1 && k0 == 1;
@@ -962,7 +970,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             const bool ghost_hi = !pk && kL == nk;
             // ---- load + primitives of plane kL on R2 ----
             if (!ghost_hi) {
-                const int gkL = map_idx(kL, nk, pk);
+                const int gkL = gkLm;
                 bool from_box = false;
                 if (tmap) {
                     // the box of this plane (issued one iteration earlier); a
@@ -977,7 +985,7 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                         pend = true;
                     }
                 }
-                const int sb = rslot<NRING>(kL) * N2;
+                const int sb = sLr * N2;
                 const int pofs = gkL * plane;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
@@ -1023,14 +1031,14 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             // iteration's updated points (plane kL - 2), waited for before
             // the update; each thread copies, and later reads, its own values
             if constexpr (!SEP) {
-                if (kL >= k0 - 1 && kL <= k1) fetch_met(kL);
+                if (kL >= k0 - 1 && kL <= k1) fetch_met(gkLm, q3L);
             } else {
                 // the spacings of plane kL + 1 into the slot of plane kL - 3,
                 // whose last reads preceded the barrier above
                 if (tid == 0) cp_async16(S.HZ + ((kL + 1) & 3), F.h1[2] + map_idx(kL + 1, nk, pk));
             }
             if (!rhs_only && kL - 2 >= k0 && kL - 2 <= k1 - 1) {
-                const int pU = map_idx(kL - 2, nk, pk) * plane;
+                const int pU = gkUm * plane;
                 const float *Q0 = J.q[0];
                 if (outA) {
                     const int oA = CK_G(4, pU + ocolA, J.npts_pad);
@@ -1046,18 +1054,18 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             cp_async_commit();
             // W of the own column at plane k0 - 2: the outer point of the
             // chunk's first zeta interface
-            if (kL == k0) wof(CK_RING(rslot<NRING>(kL - 2) * N2 + c2), Wc);
+            if (kL == k0) wof(CK_RING(sUr * N2 + c2), Wc);
             // ---- gradients of plane kG (and of plane 0, late) ----
             if (!SEP && (do_grad || do_grad0)) cp_async_wait_prev();
-            if (do_grad0) grad(0);
-            if (do_grad) grad(kG);
+            if (do_grad0) grad(0, map_idx(0, nk, pk), r3(0), r3(-1), r3(1));
+            if (do_grad) grad(kG, gkGm, q3G, q3U, q3L);
             // ---- interfaces and update of plane kU ----
             if (kU >= k0 - 1 && kU <= k1 - 1) {
                 const bool first = kU == k0 - 1; // only the -1/2 zeta flux of the chunk
-                const int gkU = map_idx(kU, nk, pk);
-                const int sU = rslot<NRING>(kU) * N2, sUp = rslot<NRING>(kU + 1) * N2, sUpp = rslot<NRING>(kU + 2) * N2;
+                const int gkU = gkUm;
+                const int sU = sUr * N2, sUp = sGr * N2, sUpp = sLr * N2;
                 const int rU = (kU & 1), rP = ((kU + 1) & 1); // R1 tables
-                const int mU = r3(kU), mP = r3(kU + 1);       // metric tables
+                const int mU = q3U, mP = q3G;       // metric tables
                 // own points at plane kU
                 const Pts L = pts(CK_RING(sU + c2));
                 float2 WL[5];
