@@ -661,6 +661,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             tma_box_load(S.QG, tmap, tx0, jb - 2, gk, S.MBAR, G_::BOX_BYTES);
         };
         const int kfirst = k0 - 2, klast = k1 + 1;
+        // carried per iteration: grid planes of kL - 2, kL - 1, kL and the
+        // three-plane ring slot of kL
+        int gkUc = map_idx(kfirst - 2, nk, pk), gkGc = map_idx(kfirst - 1, nk, pk), gkLc = map_idx(kfirst, nk, pk);
+        int q3c = r3(kfirst);
         if (tmap) stage_box(kfirst);
 
         // ---- metric cofactors and J^-1 of grid plane gk for the own row pair
@@ -958,8 +962,8 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
             const int kG = kL - 1, kU = kL - 2;
             // slots of planes kL, kG, kU in the three-plane rings, and their
             // grid planes
-            const int q3L = r3(kL), q3G = q3L == 0 ? 2 : q3L - 1, q3U = q3L == 2 ? 0 : q3L + 1;
-            const int gkLm = map_idx(kL, nk, pk), gkGm = map_idx(kG, nk, pk), gkUm = map_idx(kU, nk, pk);
+            const int q3L = q3c, q3G = q3L == 0 ? 2 : q3L - 1, q3U = q3L == 2 ? 0 : q3L + 1;
+            const int gkLm = gkLc, gkGm = gkGc, gkUm = gkUc;
             const int sLr = NRING == 4 ? (kL & 3) : q3L, sGr = NRING == 4 ? (kG & 3) : q3G, sUr = NRING == 4 ? (kU & 3) : q3U;
             const bool do_grad = kG >= k0 - 1 && kG <= k1 && !(!pk && kG == 0);
             // the first plane of a non-periodic k axis: formed with plane 1
@@ -1255,6 +1259,10 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                                  // precede the next iteration's loads into the freed slot
             }
             rjU = rjG; // plane kG is the next iteration's kU
+            gkUc = gkGc;
+            gkGc = gkLc;
+            gkLc = map_idx(kL + 1, nk, pk);
+            q3c = q3U;
         }
     }
     cp_async_wait_all();
