@@ -1100,8 +1100,9 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                 const int oA = CK_G(4, pU + ocolA, J.npts_pad), oB = CK_G(4, pU + ocolB, J.npts_pad);
                 // zeta: R = the own column one plane up; R + 1 two planes up;
                 // L - 1 one plane down (carried, or read on the first plane).
-                // General form: evaluated first in the block of the xi and eta
-                // fluxes (independent work for the scheduler to interleave)
+                // General form: evaluated between the eta and the xi flux in one
+                // block (independent work for the scheduler to interleave; of the
+                // orders measured, eta-zeta-xi ran fastest)
                 auto zeta = [&]() {
                     const Pts R = pts(CK_RING(sUp + c2));
                     float2 WR[5], WRp[5];
@@ -1127,33 +1128,6 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
                     }
                 };
                 if (!first) {
-                    if constexpr (!SEP) zeta();
-                    // xi: R = the next column.  Lane 31's R has no R1 data: it pairs
-                    // with its own R1 cell (an unused result), so that every lane
-                    // runs the xi flux without a branch and the scheduler can
-                    // interleave it with the eta flux
-                    {
-                        const int cR = tx <= FX - 2 ? c1 + 1 : c1;
-                        const Pts R = pts(CK_RING(sU + c2 + 1));
-                        float2 WR[5], WRp[5], WLm[5];
-                        wvec(R, WR);
-                        wof(CK_RING(sU + c2 + 2), WRp);
-                        wof(CK_RING(sU + c2 - 1), WLm);
-                        Side SL, SR;
-                        side(0, rU, c1, SL);
-                        side(0, rU, cR, SR);
-                        if constexpr (SEP) {
-                            // Sa = h_y h_z, hb = average h_x, tangential 1/(4 h)
-                            const float2 Sa = mul2(hYo, bc(hZo.x));
-                            const float2 hb = bc(0.5f * (hXo.x + hXp.x));
-                            iface_sep<0>(FP, L, WL, R, WR, WLm, WRp, SL, SR, Sa, hb, rcp2(hb),
-                                         mul2(bc(0.25f), rhYo), bc(0.25f * hZo.y), hx);
-                        } else {
-                            float2 mR[9], jR;
-                            mets(mU, cR, mR, jR);
-                            iface<0>(FP, L, WL, mL, jL, R, WR, mR, jR, WLm, WRp, SL, SR, hx);
-                        }
-                    }
                     // eta: R = (own second row, first row of the pair cell
                     // above); R + 1 = the pair cell above; L - 1 = (second row
                     // of the pair cell below, own first row)
@@ -1193,6 +1167,33 @@ __global__ void __launch_bounds__(FX * TY / 2, 1)
 #pragma unroll
                             for (int t = 0; t < 9; ++t) mR[t] = odd2(mL[t], mA[t]);
                             iface<1>(FP, L, WL, mL, jL, R, WR, mR, odd2(jL, jA), WLm, WP1, SL, SR, hy);
+                        }
+                    }
+                    if constexpr (!SEP) zeta();
+                    // xi: R = the next column.  Lane 31's R has no R1 data: it pairs
+                    // with its own R1 cell (an unused result), so that every lane
+                    // runs the xi flux without a branch and the scheduler can
+                    // interleave it with the eta flux
+                    {
+                        const int cR = tx <= FX - 2 ? c1 + 1 : c1;
+                        const Pts R = pts(CK_RING(sU + c2 + 1));
+                        float2 WR[5], WRp[5], WLm[5];
+                        wvec(R, WR);
+                        wof(CK_RING(sU + c2 + 2), WRp);
+                        wof(CK_RING(sU + c2 - 1), WLm);
+                        Side SL, SR;
+                        side(0, rU, c1, SL);
+                        side(0, rU, cR, SR);
+                        if constexpr (SEP) {
+                            // Sa = h_y h_z, hb = average h_x, tangential 1/(4 h)
+                            const float2 Sa = mul2(hYo, bc(hZo.x));
+                            const float2 hb = bc(0.5f * (hXo.x + hXp.x));
+                            iface_sep<0>(FP, L, WL, R, WR, WLm, WRp, SL, SR, Sa, hb, rcp2(hb),
+                                         mul2(bc(0.25f), rhYo), bc(0.25f * hZo.y), hx);
+                        } else {
+                            float2 mR[9], jR;
+                            mets(mU, cR, mR, jR);
+                            iface<0>(FP, L, WL, mL, jL, R, WR, mR, jR, WLm, WRp, SL, SR, hx);
                         }
                     }
 #pragma unroll
