@@ -59,10 +59,10 @@ TRAFFIC_BYTES_PER_POINT = {  # (workload, precision, kernel, decomposition) -> (
     # profiles/stage_kernels_fp64_jet-384x256x144.md: 13410.7 + 1682.1 MB per launch
     (_PAPER_JET, "fp64", "k_iface", None): (1066.19, "f5518e02ae9e3898"),
     # profiles/fused_stage_fp32_jet-384x256x144.md and ..._separable_...
-    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.36, "86917e2dacb050e5"),
-    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.66, "86917e2dacb050e5"),
-    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=balanced"): (77.25, "86917e2dacb050e5"),
-    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): (55.82, "86917e2dacb050e5"),
+    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.55, "2231f6aa9a29f415"),
+    (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.47, "2231f6aa9a29f415"),
+    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=balanced"): (77.23, "2231f6aa9a29f415"),
+    (_PAPER_JET, "fp32-sep", "k_fused", "ty=16 kc=lockstep"): (55.67, "2231f6aa9a29f415"),
 }
 
 
@@ -103,12 +103,12 @@ PIPE_UTIL_NCU = {  # (precision, kernel) -> (metrics dict, source sha16)
     ("fp64", "k_iface"): ({"fp64_pipe_pct": 88.58, "executed_fp64_flop_per_point": 459.8,
                           "dadd_dmul_dfma_per_point": [121.9, 70.4, 133.8]}, "f5518e02ae9e3898"),
     # profiles/fused_stage_fp32_jet-384x256x144.md (192x128x72 capture, 32x16 tiles)
-    ("fp32", "k_fused"): ({"fma_pipe_pct": 32.7, "fmaheavy_pct": 32.1, "fmalite_pct": 32.4, "issue_active_pct": 38.2,
-                          "executed_fp32_flop_per_point": 1320.6, "thread_instructions_per_point": 1157.0},
-                         "86917e2dacb050e5"),
-    ("fp32-sep", "k_fused"): ({"fma_pipe_pct": 30.3, "fmaheavy_pct": 31.8, "fmalite_pct": 28.4,
-                              "issue_active_pct": 39.2, "executed_fp32_flop_per_point": 822.0,
-                              "thread_instructions_per_point": 881.3}, "86917e2dacb050e5"),
+    ("fp32", "k_fused"): ({"fma_pipe_pct": 33.8, "fmaheavy_pct": 33.0, "fmalite_pct": 34.0, "issue_active_pct": 37.8,
+                          "executed_fp32_flop_per_point": 1320.6, "thread_instructions_per_point": 1087.1},
+                         "2231f6aa9a29f415"),
+    ("fp32-sep", "k_fused"): ({"fma_pipe_pct": 32.6, "fmaheavy_pct": 34.7, "fmalite_pct": 30.1,
+                              "issue_active_pct": 40.5, "executed_fp32_flop_per_point": 819.8,
+                              "thread_instructions_per_point": 858.0}, "2231f6aa9a29f415"),
 }
 # Nominal multiply-add throughput of GB300 (unit counts x the maximum clock),
 # reported beside the measured figures: 2 DFMA and 128 FFMA per clock and SM.
