@@ -3,9 +3,11 @@ acoustics: a point monopole and a point dipole inside a closed sphere of
 panels must give, at an outside observer, the pressure their exact fields
 radiate there; the result must not depend on the surface; the ambient at
 rest is silent; the discrete derivative and the retarded interpolation are
-exact on the polynomials of their order.  The sound speed is not 1 and the
-source sits off the sphere's centre, so that a dropped 1/c0, a wrong sign of
-the retarded time or of r, or a missing term does not cancel."""
+exact on the polynomials of their order; and the quadratic momentum-flux
+term, which the linear fields leave out, against the closed form of a steady
+uniform stream through the sphere.  The sound speed is not 1 and the source
+sits off the sphere's centre, so that a dropped 1/c0, a wrong sign of the
+retarded time or of r, or a missing term does not cancel."""
 import numpy as np
 import pytest
 
@@ -147,3 +149,34 @@ def test_derivative_and_retarded_interpolation_orders():
     s = np.array([[0.0, 10.999], [3.25, 7.5]])
     np.testing.assert_allclose(fwh.retarded(G, s), np.stack([4.0 - 2.5 * 0.3 * s[:, 0], 0.3 * s[:, 1]]).T,
                                atol=1e-12)
+
+
+@pytest.mark.parametrize("U", [np.array([0.3, 0.0, 0.0]), np.array([0.1, -0.2, 0.25])])
+def test_quadratic_momentum_flux_of_a_steady_uniform_stream(U):
+    """The quadratic source term rho u_i (u . n), which linear acoustics leaves
+    out: a steady uniform stream U through a sphere of radius a (p = p0) has
+    dQ/dtau = dL/dtau = 0, so 4 pi p' = sum A L_r / r^2 with L = rho U (U . n).
+    By the divergence theorem and the mean-value property of the harmonic
+    function (U . grad_y)^2 (1/|x - y|), the surface integral equals the
+    sphere's volume times that function at the centre:
+        p' = rho a^3 / 3 * (3 (U . d)^2 - |d|^2 |U|^2) / |d|^5,  d = x - centre.
+    Swapping u_i for n_i in the term, dropping u . n, or a wrong power of r
+    fails it; second order in the panel size."""
+    a = 1.0
+    obs = np.array([[2.5, 1.0, -0.7], [0.4, -2.2, 1.9]]).T
+    d = obs
+    R = np.sqrt((d * d).sum(axis=0))
+    exact = RHO0 * a ** 3 / 3.0 * (3.0 * (U @ d) ** 2 - R ** 2 * (U @ U)) / R ** 5
+    errs = []
+    for nth, nph in ((24, 48), (48, 96)):
+        xyz, nrm, area = sphere(a, nth, nph)
+        fr = np.empty((12, 5, xyz.shape[1]))
+        fr[:, 0] = RHO0
+        fr[:, 1:4] = U[None, :, None]
+        fr[:, 4] = P0
+        got = fwh.pressure(fr, xyz, nrm, area, DTAU, RHO0, P0, C0, obs, 0.1 + R.max() / C0, DTAU, 3)
+        # steady: every observer time gives the same value
+        np.testing.assert_allclose(got, got[:, :1].repeat(3, axis=1), rtol=1e-13, atol=0.0)
+        errs.append(np.abs(got[:, 0] - exact).max() / np.abs(exact).max())
+    assert errs[1] < 2e-4, errs
+    assert errs[1] < 0.35 * errs[0], errs
