@@ -1,9 +1,10 @@
 """FW-H far-field pressure on the GPU (les_fwh) against the oracle
 (oracle/fwh.py) element by element: on the exact field of a point monopole
 (either ring precision, a wrapped ring; the staged observer pass and, for
-observer times far apart, the direct one), on the probe frames of an LES jet
-run (real flow through the surface, so the quadratic momentum-flux term
-counts), bit-identical reruns, and the refused inputs."""
+observer times far apart, the direct one), on a steady uniform stream (the
+quadratic momentum-flux term alone, against its closed form as well), on the
+probe frames of an LES jet run (real flow through the surface), bit-identical
+reruns, and the refused inputs."""
 import numpy as np
 import pytest
 
@@ -159,3 +160,30 @@ def test_les_probe_frames_against_the_oracle():
     assert np.all(np.isfinite(got))
     assert np.abs(ref).max() > 0.0
     assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [les.LES_FP64, les.LES_FP32])
+def test_steady_uniform_stream_quadratic_term(prec):
+    """A steady uniform stream through a sphere: only the quadratic
+    momentum-flux term radiates, 4 pi p' = sum A rho (U.n)(U.r)/r^2, whose
+    closed form is rho a^3 (3 (U.d)^2 - |d|^2 |U|^2) / (3 |d|^5); the GPU
+    against the oracle and against that value."""
+    import torch
+    U = np.array([0.1, -0.2, 0.25])
+    xyz, nrm, area = _sphere(1.0, 48, 96)
+    nfr, dtau = 80, 0.05
+    frames = np.empty((nfr, 5, xyz.shape[1]))
+    frames[:, 0] = RHO0
+    frames[:, 1:4] = U[None, :, None]
+    frames[:, 4] = P0
+    ring = _ring(frames, nfr, torch.float64 if prec == les.LES_FP64 else torch.float32)
+    obs = np.array([[2.5, 1.0, -0.7], [0.4, -2.2, 1.9]]).T
+    R = np.sqrt((obs * obs).sum(axis=0))
+    t0 = (R.max() + 1.0) / C0 + 0.1          # emission times of every panel inside the 80 frames
+    got = les.les_fwh(ring.data_ptr(), prec, nfr, nfr, xyz, nrm, area, dtau, P0, C0, obs, t0, dtau, 8)
+    used = frames if prec == les.LES_FP64 else frames.astype(np.float32).astype(np.float64)
+    ref = fwh.pressure(used, xyz, nrm, area, dtau, RHO0, P0, C0, obs, t0, dtau, 8)
+    exact = RHO0 / 3.0 * (3.0 * (U @ obs) ** 2 - R ** 2 * (U @ U)) / R ** 5
+    scale = np.abs(exact).max()
+    assert np.abs(got - ref).max() <= 2e-5 * scale, np.abs(got - ref).max() / scale
+    assert np.abs(got - exact[:, None]).max() <= 2e-4 * scale
