@@ -56,8 +56,8 @@ ALGO_BYTES_PER_PT_STAGE = {"fp64": 24 * 8, "fp32": 24 * 4,
 _PAPER_JET = "jet-384x256x144"
 KERNEL_SOURCE = {"k_iface": "les_stage.cu", "k_fused": "les_fused.cu"}
 TRAFFIC_BYTES_PER_POINT = {  # (workload, precision, kernel, decomposition) -> (bytes per point, source sha16)
-    # profiles/stage_kernels_fp64_jet-384x256x144.md: 13410.7 + 1682.1 MB per launch
-    (_PAPER_JET, "fp64", "k_iface", None): (1066.19, "f5518e02ae9e3898"),
+    # profiles/stage_kernels_fp64_jet-384x256x144.md: 13415.1 + 1682.3 MB per launch
+    (_PAPER_JET, "fp64", "k_iface", None): (1066.51, "e93049f182835582"),
     # profiles/fused_stage_fp32_jet-384x256x144.md and ..._separable_...
     (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=balanced"): (128.55, "2231f6aa9a29f415"),
     (_PAPER_JET, "fp32", "k_fused", "ty=16 kc=lockstep"): (106.47, "2231f6aa9a29f415"),
@@ -100,8 +100,8 @@ def traffic_bytes_per_point(workload: str, prec: str, kname: str, describe: str,
 # the source hash of the captured kernel as above
 PIPE_UTIL_NCU = {  # (precision, kernel) -> (metrics dict, source sha16)
     # profiles/stage_kernels_fp64_jet-384x256x144.md (192x128x72 capture)
-    ("fp64", "k_iface"): ({"fp64_pipe_pct": 88.58, "executed_fp64_flop_per_point": 459.8,
-                          "dadd_dmul_dfma_per_point": [121.9, 70.4, 133.8]}, "f5518e02ae9e3898"),
+    ("fp64", "k_iface"): ({"fp64_pipe_pct": 88.82, "executed_fp64_flop_per_point": 459.8,
+                          "dadd_dmul_dfma_per_point": [118.9, 67.4, 136.8]}, "e93049f182835582"),
     # profiles/fused_stage_fp32_jet-384x256x144.md (192x128x72 capture, 32x16 tiles)
     ("fp32", "k_fused"): ({"fma_pipe_pct": 33.8, "fmaheavy_pct": 33.0, "fmalite_pct": 34.0, "issue_active_pct": 37.8,
                           "executed_fp32_flop_per_point": 1320.6, "thread_instructions_per_point": 1087.1},

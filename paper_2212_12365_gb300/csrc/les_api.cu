@@ -344,6 +344,8 @@ template <typename real> static void fill_jetdev(const les_handle *h, const JetH
     D.k2 = p.k2;
     D.k4 = p.k4;
     D.suth_S = p.S1_dim / (p.TR * p.T_inf_dim);
+    D.gm1 = p.gamma - 1.0;
+    D.suth1 = 1.0 + D.suth_S;
     D.inv_Re = 1.0 / p.Re;
     D.kap_mol = 1.0 / (p.Re * p.Pr * (p.gamma - 1.0));
     D.kap_sgs = 1.0 / (p.Pr_sgs * (p.gamma - 1.0));

@@ -80,6 +80,7 @@ struct JetDev {
     const double *inflow_ut; // nj*nk: inflow profile u~(r) of the i = 0 face points (host tanh)
     // flow parameters (jet units)
     double gamma, Pr, Pr_sgs, Re, mach, TR, theta, noise_amp, k2, k4, suth_S;
+    double gm1, suth1; // gamma - 1, 1 + suth_S
     double inv_Re;     // 1/Re (0 for an inviscid run)
     double kap_mol;    // mu -> conductivity: 1/(Re Pr (gamma-1))
     double kap_sgs;    // mu_sgs -> conductivity: 1/(Pr_sgs (gamma-1))

@@ -90,11 +90,15 @@ __global__ void __launch_bounds__(BLOCK) k_point(const JetDev<real> *__restrict_
         const real e = Q[4 * fs + lp] * rq;
         const real rrho = rcp_<real>(rho);
         const real u = ru * rrho, v = rv * rrho, w = rw * rrho;
-        const real p = (gam - real(1)) * (e - real(0.5) * (ru * u + rv * v + rw * w));
+        // gamma - 1 and 1 + S from the stored FP64 constants (the values this
+        // pass would form; the FP32 instantiation keeps its own rounding)
+        const bool f64 = sizeof(real) == sizeof(double);
+        const real gm1 = f64 ? (real)J.gm1 : gam - real(1);
+        const real p = gm1 * (e - real(0.5) * (ru * u + rv * v + rw * w));
         const real T = gam * p * rrho;
         const real sT = sqrt(T); // speed of sound: c^2 = gamma p / rho = T in jet units
         const real S = (real)J.suth_S;
-        const real mu = T * sT * (real(1) + S) * rcp1_<real>(T + S);
+        const real mu = T * sT * (f64 ? (real)J.suth1 : real(1) + S) * rcp1_<real>(T + S);
         const real rH = e + p;
         real lam[3];
         const real hp = real(0.5) * p;
@@ -324,12 +328,11 @@ __device__ __forceinline__ void iface_flux(const JetDev<real> &J, const int qL[3
         sv[i] = ch * (X[i] + Y) - ct * mr[i];
         H[1 + i] -= sv[i];
     }
-    // beta = tau u - q, q = -kappa grad T; interface velocity = average
-    const real fe = real(0.5) * ((P[P_U * fs + L] + P[P_U * fs + R]) * sv[0] +
-                                 (P[P_V * fs + L] + P[P_V * fs + R]) * sv[1] +
-                                 (P[P_W * fs + L] + P[P_W * fs + R]) * sv[2]) +
-                    kap * X[3];
-    H[4] -= fe;
+    // beta = tau u - q, q = -kappa grad T; interface velocity = average:
+    // H4 -= 1/2 sum_i (u_i,L + u_i,R) s_i + kappa X_T, as two multiply-adds
+    const real su = (P[P_U * fs + L] + P[P_U * fs + R]) * sv[0] + (P[P_V * fs + L] + P[P_V * fs + R]) * sv[1] +
+                    (P[P_W * fs + L] + P[P_W * fs + R]) * sv[2];
+    H[4] = fma(-kap, X[3], fma(real(-0.5), su, H[4]));
 }
 
 template <typename real>
